@@ -1,0 +1,513 @@
+#!/usr/bin/env python
+"""Benchmark of the batched big-integer hot path on GB300.
+
+One step = one pass of every step of the path over its synthetic batch:
+  * add, sub and full-product mul at 2^15 .. 2^19 bits (512 .. 8192 limbs),
+    each operand array 2^32 bits (batch 2^26 / n) -- the paper's
+    Bits x Insts = 2^32 size sweep (Sec. VI, Tables I and II);
+  * divmod of a 2n-limb dividend by an n-limb divisor at n = 512, 2048, 8192
+    (batches 4096, 1024, 256) -- Newton shifted-inverse division (Table III).
+The headline value is limb-Gops/s: output limbs for add/sub, limb products
+(n_a n_b) for mul, (n_u - n_v + 1) n_v limb-product equivalents for divmod,
+summed over the step and divided by the device time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 run under torch.distributed.run; every rank processes the same
+per-GPU batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import platform
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("bigint mul & divmod ops/s and limb-Gops/s at 2^15–2^19 bits; "
+          "% of int-mul/HBM peak")
+UNIT = "limb-Gops/s"
+SWEEP = (512, 1024, 2048, 4096, 8192)
+DIV = ((512, 4096), (2048, 1024), (8192, 256))
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sizes", default=",".join(str(n) for n in SWEEP))
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# workload accounting (shared by both arms)
+# --------------------------------------------------------------------------
+def sweep_batch(n: int) -> int:
+    return (1 << 26) // n
+
+
+def step_units(sizes):
+    """(name, batch, limb-ops per instance) of every op in one step."""
+    ops = []
+    for n in sizes:
+        b = sweep_batch(n)
+        ops.append((f"add_{n}", b, n))
+        ops.append((f"sub_{n}", b, n))
+        ops.append((f"mul_{n}", b, n * n))
+    for n, b in DIV:
+        ops.append((f"divmod_{2 * n}_{n}", b, (n + 1) * n))
+    return ops
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 8]
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax = max(smax, float(r[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[4:8]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the same workload
+# --------------------------------------------------------------------------
+def oracle_sample_rate(sizes, budget_s: float):
+    """Times the plain CPU oracle on a bounded sample of every op of the step,
+    extrapolates the time of a full step, and returns the limb-Gops/s a full
+    step would reach, the host threads used and a description."""
+    import numpy as np
+
+    import oracle
+    from paper_2607_28897_gb300 import inputs
+
+    oracle.build()
+    ops = step_units(sizes)
+    per_op = budget_s / len(ops)
+    total_ops, total_time, desc = 0.0, 0.0, []
+    for name, batch, units in ops:
+        kind = name.split("_")[0]
+        if kind == "divmod":
+            n = int(name.split("_")[2])
+        else:
+            n = int(name.split("_")[1])
+        k = 1
+        while True:
+            k = min(k, batch)
+            if kind == "divmod":
+                u, v = inputs.config_div(n, k)
+                t0 = time.perf_counter()
+                oracle.batch_divmod(u, v)
+            else:
+                a = inputs.limbs(11 + n, k, n, True)
+                b = inputs.limbs(12 + n, k, n, True)
+                t0 = time.perf_counter()
+                if kind == "add":
+                    oracle.batch_add(a, b)
+                elif kind == "sub":
+                    oracle.batch_sub(a, b)
+                else:
+                    oracle.batch_mul(a, b)
+            dt = time.perf_counter() - t0
+            if dt >= per_op or k >= batch or dt * (2 * batch / k) < 0.05:
+                break
+            k = int(min(batch, max(2 * k, k * per_op / max(dt, 1e-6) * 0.8)))
+        full = dt * batch / k
+        total_ops += batch * units
+        total_time += full
+        desc.append(f"{name}:{k}/{batch}")
+    return total_ops / total_time / 1e9, oracle.num_threads(), " ".join(desc)
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+# --------------------------------------------------------------------------
+# committed ncu traffic of the multiply kernel, valid only for its source
+# --------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mulcore.cuh", "mul.cu", "blockops.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2607_28897_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    path = os.path.join(ROOT, "profiles", "mul_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle, K timed steps of a bounded sample
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sizes = [int(s) for s in args.sizes.split(",")]
+    for _ in range(args.warmup):
+        oracle_sample_rate(sizes, 2.0)
+    vals, t0 = [], time.perf_counter()
+    threads, desc = 1, ""
+    for _ in range(args.steps):
+        v, threads, desc = oracle_sample_rate(sizes, 8.0)
+        vals.append(v)
+    elapsed = time.perf_counter() - t0
+    value = sum(vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed * 1e3 / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(sizes),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc, "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(sizes):
+    return {
+        "workload": ("add/sub/mul sweep at 2^15..2^19 bits, 2^32 bits per operand array "
+                     "(batch 2^26/n), + divmod 2n/n limbs at n=512/2048/8192 "
+                     "(batch 4096/1024/256)"),
+        "sweep_limbs": list(sizes),
+        "div": [list(d) for d in DIV],
+        "l2": "sweep operands (512 MiB each) exceed L2; L2 flushed (256 MiB write) before each step",
+        "parallelism": "instances: one CTA per instance, batches sharded per GPU",
+    }
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    bi.load()
+    sizes = [int(s) for s in args.sizes.split(",")]
+
+    # ---- inputs, resident in HBM before timing (seeded, per rank)
+    seed_off = 1000 * rank
+    sweep = {}
+    for n in sizes:
+        a, b = inputs.config_sweep_torch(n, seed=2 + seed_off, device=dev)
+        # subtraction operands ordered a >= b (top limbs decide for random data)
+        top_a = a[:, -1] ^ (-(1 << 63))  # unsigned order as signed order
+        top_b = b[:, -1] ^ (-(1 << 63))
+        sw = top_a < top_b
+        sa = torch.where(sw[:, None], b, a)
+        sb = torch.where(sw[:, None], a, b)
+        batch = a.shape[0]
+        sweep[n] = dict(a=a, b=b, sa=sa, sb=sb,
+                        s=torch.empty_like(a), d=torch.empty_like(a),
+                        p=torch.empty((batch, 2 * n), dtype=torch.int64, device=dev),
+                        c=torch.empty(batch, dtype=torch.uint8, device=dev))
+    import numpy as np
+
+    divs = {}
+    for n, batch in DIV:
+        u, v = inputs.config_div(n, batch, seed=3 + seed_off)
+        du = torch.from_numpy(u.view(np.int64)).to(dev)
+        dv = torch.from_numpy(v.view(np.int64)).to(dev)
+        ws = torch.empty(bi.divmod_workspace_bytes(batch, 2 * n, n), dtype=torch.uint8, device=dev)
+        divs[n] = dict(u=du, v=dv, ws=ws,
+                       q=torch.empty((batch, n + 1), dtype=torch.int64, device=dev),
+                       r=torch.empty((batch, n), dtype=torch.int64, device=dev),
+                       st=torch.empty(batch, dtype=torch.int32, device=dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    mul_events = {n: [] for n in sizes}
+    add_events = {n: [] for n in sizes}
+
+    def one_step(record):
+        launches = 0
+        flush.fill_(1)
+        for n in sizes:
+            S = sweep[n]
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            bi.add(S["a"], S["b"], out=S["s"], carry=S["c"])
+            if record:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                add_events[n].append((e0, e1))
+            bi.sub(S["sa"], S["sb"], out=S["d"], borrow=S["c"])
+            if record:
+                e2 = torch.cuda.Event(enable_timing=True)
+                e2.record(stream)
+            bi.mul(S["a"], S["b"], out=S["p"])
+            if record:
+                e3 = torch.cuda.Event(enable_timing=True)
+                e3.record(stream)
+                mul_events[n].append((e2, e3))
+            launches += 3
+        for n, batch in DIV:
+            D = divs[n]
+            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"])
+            launches += 1
+        return launches
+
+    for _ in range(max(args.warmup, 3)):
+        one_step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        launches += one_step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ops = step_units(sizes)
+    limb_ops_step = sum(b * u for _, b, u in ops)
+    value = world * limb_ops_step * args.steps / (ms_total * 1e-3) / 1e9
+
+    # ---- per-op breakdown from a separately timed pass (one launch each)
+    breakdown = {}
+
+    def time_op(fn, reps=1):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        s0.record(stream)
+        for _ in range(reps):
+            fn()
+        s1.record(stream)
+        s1.synchronize()
+        return s0.elapsed_time(s1) / reps
+
+    for n in sizes:
+        S = sweep[n]
+        b = S["a"].shape[0]
+        t_add = sum(e0.elapsed_time(e1) for e0, e1 in add_events[n]) / len(add_events[n])
+        t_mul = sum(e0.elapsed_time(e1) for e0, e1 in mul_events[n]) / len(mul_events[n])
+        breakdown[f"add_{n}"] = {"ms": t_add, "ops_per_s": b / (t_add * 1e-3),
+                                 "GB_s": 24.0 * b * n / (t_add * 1e-3) / 1e9}
+        breakdown[f"mul_{n}"] = {"ms": t_mul, "ops_per_s": b / (t_mul * 1e-3),
+                                 "limb_gops": b * n * n / (t_mul * 1e-3) / 1e9}
+    for n, batch in DIV:
+        D = divs[n]
+        t = time_op(lambda: bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"],
+                                      workspace=D["ws"]))
+        breakdown[f"divmod_{2 * n}_{n}"] = {"ms": t, "ops_per_s": batch / (t * 1e-3),
+                                            "limb_gops": batch * (n + 1) * n / (t * 1e-3) / 1e9}
+
+    # ---- roofline of the dominant kernel (the multiply)
+    ipc, probe_mhz = bi.probe_int_throughput(0)  # IMAD.WIDE per SM per clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk["sm_mhz"] if clk else probe_mhz
+    peak = ipc * sms * mhz * 1e6 / 1e12  # T IMAD.WIDE / s at the clock under load
+    mul_ms = sum(breakdown[f"mul_{n}"]["ms"] for n in sizes)
+    mul_work = sum(4.0 * sweep_batch(n) * n * n for n in sizes)  # 4 IMAD.WIDE per limb product
+    achieved = mul_work / (mul_ms * 1e-3) / 1e12
+    tr = committed_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T IMAD.WIDE-equivalent/s (4 per limb product)", "frac": achieved / peak,
+                "traffic": tr["bytes_per_launch"] if tr else None,
+                "kernel": "k_mul (all sweep sizes)",
+                "peak_basis": (f"measured {ipc:.1f} IMAD.WIDE/clk/SM x {sms} SMs x "
+                               f"{mhz:.0f} MHz (median SM clock in the timed region)")}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    add_bytes = sum(24.0 * sweep_batch(n) * n for n in sizes)
+    add_ms = sum(breakdown[f"add_{n}"]["ms"] for n in sizes)
+    roofline_add = {"bound": "hbm", "achieved": add_bytes / (add_ms * 1e-3) / 1e9,
+                    "peak": hbm_peak, "unit": "GB/s",
+                    "frac": add_bytes / (add_ms * 1e-3) / 1e9 / hbm_peak,
+                    "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+                    if "hbm_gbs" in peaks else "fallback 6800 GB/s", "kernel": "k_addsub"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, world, dist)
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, th, desc = oracle_sample_rate(sizes, 20.0)
+        cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc,
+               "cpu": cpu_model()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": workload_config(sizes), "roofline": roofline,
+            "roofline_add": roofline_add, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, world, dist):
+    """Same step through the C ABI with pinned host buffers: every input is
+    copied host->device and every result device->host inside the timed
+    region."""
+    steps = max(1, args.e2e_steps)
+    host_in = {}
+    for n in sizes:
+        S = sweep[n]
+        host_in[n] = (S["a"].cpu().pin_memory(), S["b"].cpu().pin_memory(),
+                      S["sa"].cpu().pin_memory(), S["sb"].cpu().pin_memory())
+    host_div = {n: (divs[n]["u"].cpu().pin_memory(), divs[n]["v"].cpu().pin_memory())
+                for n, _ in DIV}
+    big = max(sweep[n]["p"].numel() for n in sizes)
+    out_host = torch.empty(big, dtype=torch.int64).pin_memory()
+    h2d = d2h = 0
+    for n in sizes:
+        h2d += sum(t.numel() * 8 for t in host_in[n])
+        d2h += (sweep[n]["s"].numel() * 2 + sweep[n]["p"].numel()) * 8
+    for n, _ in DIV:
+        h2d += sum(t.numel() * 8 for t in host_div[n])
+        d2h += (divs[n]["q"].numel() + divs[n]["r"].numel()) * 8
+
+    def step():
+        for n in sizes:
+            S = sweep[n]
+            ha, hb, hsa, hsb = host_in[n]
+            S["a"].copy_(ha, non_blocking=True)
+            S["b"].copy_(hb, non_blocking=True)
+            bi.add(S["a"], S["b"], out=S["s"], carry=S["c"])
+            out_host[: S["s"].numel()].copy_(S["s"].view(-1), non_blocking=True)
+            S["sa"].copy_(hsa, non_blocking=True)
+            S["sb"].copy_(hsb, non_blocking=True)
+            bi.sub(S["sa"], S["sb"], out=S["d"], borrow=S["c"])
+            out_host[: S["d"].numel()].copy_(S["d"].view(-1), non_blocking=True)
+            bi.mul(S["a"], S["b"], out=S["p"])
+            out_host[: S["p"].numel()].copy_(S["p"].view(-1), non_blocking=True)
+        for n, _ in DIV:
+            D = divs[n]
+            hu, hv = host_div[n]
+            D["u"].copy_(hu, non_blocking=True)
+            D["v"].copy_(hv, non_blocking=True)
+            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"])
+            out_host[: D["q"].numel()].copy_(D["q"].view(-1), non_blocking=True)
+            out_host[: D["r"].numel()].copy_(D["r"].view(-1), non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

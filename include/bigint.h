@@ -1,0 +1,153 @@
+/*
+ * bigint.h -- C ABI of libbigint: batched exact arithmetic on midsize
+ * unsigned integers on one GB300 (sm_103a).
+ *
+ * Method: "High-Level Big Integer Arithmetic in Futhark for GPUs"
+ * (Oancea and Watt).  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - An integer is an array of 64-bit limbs, least significant first
+ *   (Sec. II: M digits of base B = 2^b, little-endian; Sec. VI: b = 64).
+ * - A uniform batch of `count` instances of `n` limbs is one contiguous
+ *   array of count*n limbs, instance i at offset i*n (instance-major).
+ * - All data pointers are DEVICE pointers owned by the caller.  The library
+ *   never frees them and keeps no reference after the call returns.
+ * - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
+ *   void*; NULL is the legacy default stream).  Output buffers must not
+ *   overlap input buffers.
+ * - Return value: BIGINT_OK or a negative error code.  Argument errors are
+ *   detected on the host before anything is launched.  Per-instance
+ *   conditions (division by zero, quotient overflow) are reported through
+ *   per-instance status arrays and never abort the batch.
+ */
+#ifndef BIGINT_H
+#define BIGINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------*/
+#define BIGINT_OK 0
+#define BIGINT_EINVAL (-1)     /* bad argument (sizes, NULL, alignment)       */
+#define BIGINT_EDIVZERO (-2)   /* per instance: divisor is zero               */
+#define BIGINT_ENOMEM (-3)     /* workspace too small                         */
+#define BIGINT_ETIMEOUT (-4)   /* a device-side wait hit its iteration limit  */
+#define BIGINT_EINTERNAL (-5)  /* an internal correction limit was exceeded   */
+#define BIGINT_ECUDA (-6)      /* a CUDA runtime call failed                  */
+#define BIGINT_ERANGE (-7)     /* per instance: quotient does not fit in nq   */
+
+/* Largest operand accepted by add, sub and divmod, in limbs (2^20 bits). */
+#define BIGINT_MAX_LIMBS 16384
+/* Largest operand accepted by mul and mul_lo, in limbs (both operands of
+ * one product are held in one SM's shared memory). */
+#define BIGINT_MUL_MAX_LIMBS 10000
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *bigint_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int bigint_version(void);
+
+/* ---- addition and subtraction (Sec. V-A, Figs. 3 and 4) -----------------
+ * out = (a + b) mod B^n, carry_out[i] = floor((a_i + b_i) / B^n) in {0,1}.
+ * The carry is propagated as an exclusive scan over per-digit
+ * (generate, propagate) pairs with the operator
+ *   (g1,p1) o (g2,p2) = (g2 | (g1 & p2), p1 & p2)                (Fig. 3)
+ * blocked as in Fig. 4: each thread folds its own limbs sequentially, then
+ * a block-level scan joins the threads.
+ * a, b, out: count*n limbs.  carry_out: count bytes, or NULL.
+ * 1 <= n <= BIGINT_MAX_LIMBS, count >= 0 (count == 0 is a no-op).      */
+int bigint_add(const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint8_t *carry_out, int64_t count, int32_t n, void *stream);
+
+/* out = (a - b) mod B^n, borrow_out[i] = 1 iff a_i < b_i.  Subtraction is
+ * named but not shown in the paper (Sec. V-C uses bsubReg); it is the same
+ * scan with generate = (a_j < b_j) and propagate = (a_j == b_j).
+ * Same layout and limits as bigint_add.                                  */
+int bigint_sub(const uint64_t *a, const uint64_t *b, uint64_t *out,
+               uint8_t *borrow_out, int64_t count, int32_t n, void *stream);
+
+/* ---- multiplication (Sec. V-B, Fig. 5) ----------------------------------
+ * out = a * b, the FULL product of na + nb limbs per instance.  The
+ * convolution C_k = sum_{i+j=k} a_i b_j is computed column-block by
+ * column-block with a balanced assignment of column blocks to threads
+ * (Fig. 5 threadConv), each block accumulated as (Q digits, high, carry)
+ * (Fig. 5 combineQ); the per-block overflow words are then added in by one
+ * carry-scan addition (Fig. 5 bmulReg).
+ * a: count*na limbs, b: count*nb limbs, out: count*(na+nb) limbs.
+ * 1 <= na, nb <= BIGINT_MUL_MAX_LIMBS.                                     */
+int bigint_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
+               int64_t count, int32_t na, int32_t nb, void *stream);
+
+/* Low m limbs of a*b (the product modulo B^m): the variable-precision
+ * multiply of Sec. V-C, Fig. 6 (varPrecMul, "computes the first m digits
+ * of A*B").  a: count*na, b: count*nb, out: count*m limbs,
+ * 1 <= na, nb <= BIGINT_MUL_MAX_LIMBS, 1 <= m <= na + nb.                 */
+int bigint_mul_lo(const uint64_t *a, const uint64_t *b, uint64_t *out,
+                  int64_t count, int32_t na, int32_t nb, int32_t m,
+                  void *stream);
+
+/* ---- division (Sec. V-C, Fig. 6) ----------------------------------------
+ * q = floor(u / v), r = u - q v, by the shifted inverse
+ *   w = shinv_h(v) = floor(B^h / v)
+ * computed with Newton steps (Fig. 6 `step`) over variable-precision
+ * multiplications, followed by q = floor(u w / B^h) with an exact final
+ * correction.
+ * u: count*nu limbs, v: count*nv limbs, q: count*nq limbs with
+ * nq = max(nu - nv + 1, 1), r: count*nv limbs, status: count int32 (may be
+ * NULL): 0, BIGINT_EDIVZERO (v = 0; q and r are set to 0) or BIGINT_ERANGE
+ * (v has leading zero limbs and the quotient needs more than nq limbs; q
+ * holds the quotient mod B^nq and r is exact).
+ * workspace: device scratch of at least bigint_divmod_workspace(count, nu,
+ * nv) bytes, 256-byte aligned, owned by the caller, contents clobbered.
+ * 1 <= nu, nv <= BIGINT_MAX_LIMBS.                                        */
+int bigint_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q,
+                  uint64_t *r, int32_t *status, int64_t count, int32_t nu,
+                  int32_t nv, void *workspace, size_t workspace_bytes,
+                  void *stream);
+
+/* Bytes of device workspace bigint_divmod needs for this batch shape. */
+size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv);
+
+/* Shifted inverse w = floor(B^h / v) (Sec. V-C; the Newton loop of Fig. 6).
+ * v: count*nv limbs, w: count*nw limbs.  status as for bigint_divmod
+ * (BIGINT_ERANGE if the inverse needs more than nw limbs).
+ * nv <= h <= 2*BIGINT_MAX_LIMBS.  workspace: bigint_shinv_workspace bytes. */
+int bigint_shinv(const uint64_t *v, uint64_t *w, int32_t *status,
+                 int64_t count, int32_t nv, int32_t h, int32_t nw,
+                 void *workspace, size_t workspace_bytes, void *stream);
+size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h);
+
+/* ---- tuning and measurement ---------------------------------------------
+ * Selects the kernel variant an operation uses from now on (process-wide,
+ * not thread-safe; call it before launching work).  op 0 = multiply:
+ *   variant 0 (default): 28-bit digits, 8-column chunks, carries every 128 rows
+ *   variant 1: 28-bit digits, 16-column chunks, carries every 128 rows
+ *   variant 2: 29-bit digits, 8-column chunks, carries every 32 rows
+ *   variant 3: 30-bit digits, 8-column chunks, carries every 8 rows
+ * Returns BIGINT_EINVAL for an unknown op or variant.                      */
+int bigint_set_variant(int op, int variant);
+
+/* Integer-pipe throughput probe used for the multiply roofline: every SM
+ * runs a register-only loop of one instruction form at full occupancy and
+ * times itself with the SM cycle counter.  Returns thread-level operations
+ * per SM per SM clock cycle (*ops_per_clk_sm) and the SM clock seen
+ * (*sm_mhz).
+ *   variant 0: 32x32->64-bit multiply-add (mad.wide.u32, IMAD.WIDE)
+ *   variant 1: 32-bit multiply-add, low half (mad.lo.u32)
+ *   variant 2: 32-bit multiply-add, high half (mad.hi.u32)
+ *   variant 3: the multiply kernel's inner step (one mad.wide.u32 per digit
+ *              product into 8 column accumulators), ops = digit products
+ * Synchronous; allocates two small device buffers for the duration.       */
+int bigint_probe_int_throughput(int variant, double *ops_per_clk_sm,
+                                double *sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIGINT_H */

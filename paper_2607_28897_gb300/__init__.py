@@ -1,0 +1,235 @@
+"""Batched exact arithmetic on midsize unsigned integers on one GB300.
+
+Thin Python binding over the C ABI of ``libbigint.so`` (``include/bigint.h``):
+argument marshalling only.  Every arithmetic step runs in the CUDA kernels of
+``csrc/``; PyTorch is used for device memory and streams.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls raise.
+
+Integers are little-endian arrays of 64-bit limbs.  A batch is a CUDA tensor
+of shape ``(count, n)`` and dtype ``torch.uint64`` or ``torch.int64`` (the
+bits are what matter), contiguous, instance-major.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "shinv",
+    "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
+    "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
+    "MAX_LIMBS", "MUL_MAX_LIMBS",
+]
+
+OK, EINVAL, EDIVZERO, ENOMEM, ETIMEOUT, EINTERNAL, ECUDA, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
+MAX_LIMBS = 16384
+MUL_MAX_LIMBS = 10000
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbigint.so")
+
+# Every symbol include/bigint.h declares, with its ctypes signature.
+_P, _I64, _I32, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+SIGNATURES = {
+    "bigint_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "bigint_version": ([], ctypes.c_int),
+    "bigint_add": ([_P, _P, _P, _P, _I64, _I32, _P], ctypes.c_int),
+    "bigint_sub": ([_P, _P, _P, _P, _I64, _I32, _P], ctypes.c_int),
+    "bigint_mul": ([_P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "bigint_mul_lo": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P], ctypes.c_int),
+    "bigint_divmod": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
+    "bigint_divmod_workspace": ([_I64, _I32, _I32], _SZ),
+    "bigint_shinv": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
+    "bigint_shinv_workspace": ([_I64, _I32, _I32], _SZ),
+    "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+}
+
+
+class BigIntError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbigint.so (built by ``build.py``).  Raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"libbigint.so not found at {p}: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    L = ctypes.CDLL(p)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().bigint_strerror(code).decode()
+    except Exception:  # library unavailable: still give a readable message
+        return {0: "ok", -1: "invalid argument", -2: "division by zero"}.get(code, "error")
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise BigIntError(rc, what)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dev_tensor(x, name: str):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype not in (torch.uint64, torch.int64):
+        raise TypeError(f"{name} must have dtype uint64 or int64")
+    if x.dim() != 2 or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (count, n) tensor")
+    return x
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _empty_like_limbs(ref, count: int, n: int):
+    torch = _torch()
+    return torch.empty((count, n), dtype=ref.dtype, device=ref.device)
+
+
+def add(a, b, out=None, carry=None, stream=None):
+    """(a + b) mod B^n and the carry out per instance (uint8)."""
+    return _addsub("bigint_add", a, b, out, carry, stream)
+
+
+def sub(a, b, out=None, borrow=None, stream=None):
+    """(a - b) mod B^n and the borrow out per instance (uint8, 1 iff a < b)."""
+    return _addsub("bigint_sub", a, b, out, borrow, stream)
+
+
+def _addsub(fn, a, b, out, flag, stream):
+    torch = _torch()
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    if a.shape != b.shape:
+        raise ValueError("a and b must have the same shape")
+    count, n = a.shape
+    out = _empty_like_limbs(a, count, n) if out is None else _dev_tensor(out, "out")
+    if flag is None:
+        flag = torch.empty(count, dtype=torch.uint8, device=a.device)
+    rc = getattr(load(), fn)(a.data_ptr(), b.data_ptr(), out.data_ptr(), flag.data_ptr(),
+                             count, n, _stream_ptr(stream))
+    _check(rc, fn)
+    return out, flag
+
+
+def mul(a, b, out=None, stream=None):
+    """Full product, (count, na + nb) limbs."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, na = a.shape
+    nb = b.shape[1]
+    if b.shape[0] != count:
+        raise ValueError("batch sizes differ")
+    out = _empty_like_limbs(a, count, na + nb) if out is None else _dev_tensor(out, "out")
+    rc = load().bigint_mul(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
+                           _stream_ptr(stream))
+    _check(rc, "bigint_mul")
+    return out
+
+
+def mul_lo(a, b, m: int, out=None, stream=None):
+    """Low m limbs of the product (the product mod B^m)."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, na = a.shape
+    nb = b.shape[1]
+    out = _empty_like_limbs(a, count, m) if out is None else _dev_tensor(out, "out")
+    rc = load().bigint_mul_lo(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb, m,
+                              _stream_ptr(stream))
+    _check(rc, "bigint_mul_lo")
+    return out
+
+
+def divmod_workspace_bytes(count: int, nu: int, nv: int) -> int:
+    return int(load().bigint_divmod_workspace(count, nu, nv))
+
+
+def shinv_workspace_bytes(count: int, nv: int, h: int) -> int:
+    return int(load().bigint_shinv_workspace(count, nv, h))
+
+
+def _workspace(nbytes: int, device):
+    torch = _torch()
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def divmod(u, v, q=None, r=None, status=None, workspace=None, stream=None):
+    """q = floor(u / v) ((count, max(nu-nv+1, 1)) limbs), r = u mod v
+    ((count, nv) limbs) and a per-instance int32 status."""
+    torch = _torch()
+    u, v = _dev_tensor(u, "u"), _dev_tensor(v, "v")
+    count, nu = u.shape
+    nv = v.shape[1]
+    nq = max(nu - nv + 1, 1)
+    q = _empty_like_limbs(u, count, nq) if q is None else _dev_tensor(q, "q")
+    r = _empty_like_limbs(u, count, nv) if r is None else _dev_tensor(r, "r")
+    if status is None:
+        status = torch.empty(count, dtype=torch.int32, device=u.device)
+    need = divmod_workspace_bytes(count, nu, nv)
+    if workspace is None:
+        workspace = _workspace(need, u.device)
+    rc = load().bigint_divmod(u.data_ptr(), v.data_ptr(), q.data_ptr(), r.data_ptr(),
+                              status.data_ptr(), count, nu, nv, workspace.data_ptr(),
+                              workspace.numel() * workspace.element_size(),
+                              _stream_ptr(stream))
+    _check(rc, "bigint_divmod")
+    return q, r, status
+
+
+def shinv(v, h: int, nw: int, w=None, status=None, workspace=None, stream=None):
+    """w = floor(B^h / v), (count, nw) limbs, and a per-instance status."""
+    torch = _torch()
+    v = _dev_tensor(v, "v")
+    count, nv = v.shape
+    w = _empty_like_limbs(v, count, nw) if w is None else _dev_tensor(w, "w")
+    if status is None:
+        status = torch.empty(count, dtype=torch.int32, device=v.device)
+    need = shinv_workspace_bytes(count, nv, h)
+    if workspace is None:
+        workspace = _workspace(need, v.device)
+    rc = load().bigint_shinv(v.data_ptr(), w.data_ptr(), status.data_ptr(), count, nv, h, nw,
+                             workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                             _stream_ptr(stream))
+    _check(rc, "bigint_shinv")
+    return w, status
+
+
+def set_variant(op: int, variant: int) -> None:
+    """Select the kernel variant of an operation (op 0 = multiply)."""
+    _check(load().bigint_set_variant(op, variant), "bigint_set_variant")
+
+
+def probe_int_throughput(variant: int):
+    """(thread operations per SM per cycle, SM MHz) of one integer form."""
+    ops, mhz = ctypes.c_double(), ctypes.c_double()
+    rc = load().bigint_probe_int_throughput(variant, ctypes.byref(ops), ctypes.byref(mhz))
+    _check(rc, "bigint_probe_int_throughput")
+    return ops.value, mhz.value

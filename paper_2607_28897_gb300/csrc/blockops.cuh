@@ -1,0 +1,135 @@
+// blockops.cuh -- block-level linear operations on limb arrays.
+//
+// Every routine here is executed by ALL threads of a CTA together (it
+// contains __syncthreads) and works for any blockDim.x that is a multiple of
+// 32 (up to 1024).  They are the building blocks of the multiply's final
+// addition (Sec. V-B, Fig. 5 bmulReg's baddReg) and of the division's linear
+// steps (Sec. V-C, Fig. 6: baddReg', bsubReg', baddOne, prec, shift,
+// nullUpToInd), which the paper pads to full precision.
+#pragma once
+#include "common.cuh"
+
+namespace bigint {
+
+// Shared scratch (32-bit words) the routines below need.
+constexpr int BLK_SCRATCH_WORDS = 72;
+
+// ---------------------------------------------------------------------------
+// out(j) = x(j) + y(j) (+carry) or x(j) - y(j) (-borrow), j in [0, n), in
+// limb order, with the carry/borrow scan of Fig. 3.  `load(j)` returns the
+// pair (x_j, y_j); `store(j, r)` writes the result.  Warps take contiguous
+// segments of R*32 limbs (one limb per lane per round); successive
+// super-rounds hand their carry on through shared memory.  Returns the carry
+// (borrow) out of limb n-1.  load() may read what store() wrote earlier only
+// for the same j.
+// ---------------------------------------------------------------------------
+template <bool SUB, class Load, class Store>
+__device__ uint32_t blk_addsub(int n, uint32_t cin, Load load, Store store, uint32_t *sm) {
+  constexpr int R = 4;
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t *s_g = sm, *s_p = sm + 32;
+  uint32_t c_super = cin;
+  for (int base = 0; base < n; base += nwarps * R * 32) {
+    const int wb = base + warp * R * 32;
+    uint64_t s[R];
+    uint32_t gb = 0, pb = 0;
+    WarpCarry wc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int j = wb + r * 32 + (int)lane;
+      uint32_t g = 0, p = 1;  // past the end: pass carries through
+      s[r] = 0;
+      if (j < n) {
+        const ulonglong2 xy = load(j);
+        const uint64_t t = SUB ? xy.x - xy.y : xy.x + xy.y;
+        g = SUB ? (xy.x < xy.y) : (t < xy.x);
+        p = SUB ? (t == 0) : (t == ~0ull);
+        s[r] = t;
+      }
+      gb |= g << r;
+      pb |= p << r;
+      wc[r] = warp_gp(g, p);
+    }
+    uint32_t wg = 0, wp = 1;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      wg = warp_carry_out(wc[r], 0) | (warp_all_propagate(wc[r]) & wg);
+      wp &= warp_all_propagate(wc[r]);
+    }
+    if (lane == 0) { s_g[warp] = wg; s_p[warp] = wp; }
+    __syncthreads();
+    const uint32_t gw = (int)lane < nwarps ? s_g[lane] : 0;
+    const uint32_t pw = (int)lane < nwarps ? s_p[lane] : 1;
+    const uint64_t cm = warp_carries(warp_gp(gw, pw), c_super);
+    uint32_t c = (uint32_t)(cm >> warp) & 1u;
+    const uint32_t cout = (uint32_t)(cm >> nwarps) & 1u;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint64_t lc = warp_carries(wc[r], c);
+      const uint32_t cl = (uint32_t)(lc >> lane) & 1u;
+      c = (uint32_t)(lc >> 32) & 1u;
+      const int j = wb + r * 32 + (int)lane;
+      if (j < n) store(j, SUB ? s[r] - cl : s[r] + cl);
+    }
+    c_super = cout;
+    __syncthreads();
+  }
+  return c_super;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide maximum of one int per thread (all threads get the result).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int blk_max(int v, uint32_t *sm) {
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  v = __reduce_max_sync(FULL, v);
+  int *s = reinterpret_cast<int *>(sm);
+  if (lane == 0) s[warp] = v;
+  __syncthreads();
+  int w = (int)lane < nwarps ? s[lane] : INT32_MIN;
+  w = __reduce_max_sync(FULL, w);
+  __syncthreads();
+  return w;
+}
+
+// Precision of x[0..n): index of the highest nonzero limb plus one, 0 for
+// zero (Fig. 6 prec; a block max-reduction instead of atomics).
+__device__ __forceinline__ int blk_prec(const uint64_t *x, int n, uint32_t *sm) {
+  int p = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (x[j] != 0) p = j + 1;
+  return blk_max(p, sm);
+}
+
+// dst[0..n) = src[0..n)  (no overlap).
+__device__ __forceinline__ void blk_copy(uint64_t *dst, const uint64_t *src, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+}
+
+__device__ __forceinline__ void blk_zero(uint64_t *dst, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = 0;
+}
+
+// 1 if any of x[0..n) is nonzero (Fig. 6 nullUpToInd, negated).
+__device__ __forceinline__ int blk_any_nonzero(const uint64_t *x, int n, uint32_t *sm) {
+  int f = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) f |= (x[j] != 0);
+  return blk_max(f, sm);
+}
+
+// Three-way comparison of x[0..n) and y[0..n): -1, 0, +1.
+__device__ __forceinline__ int blk_cmp(const uint64_t *x, const uint64_t *y, int n,
+                                       uint32_t *sm) {
+  int top = 0;  // highest differing index + 1
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (x[j] != y[j]) top = j + 1;
+  top = blk_max(top, sm);
+  if (top == 0) return 0;
+  return x[top - 1] > y[top - 1] ? 1 : -1;
+}
+
+}  // namespace bigint

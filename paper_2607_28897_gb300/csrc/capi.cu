@@ -1,0 +1,137 @@
+// capi.cu -- the extern "C" entry points of libbigint (include/bigint.h).
+//
+// Host-side argument checks and dispatch only; every arithmetic step runs in
+// the kernels of addsub.cu, mul.cu and divmod.cu.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace bigint {
+int launch_addsub(bool sub, const uint64_t *a, const uint64_t *b, uint64_t *out,
+                  uint8_t *carry, int64_t count, int n, cudaStream_t st);
+int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+               int nb, int nout, cudaStream_t st);
+int mul_max_limbs();
+int mul_set_variant(int v);
+int probe_int_throughput(int variant, double *ops, double *mhz);
+int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                  int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
+                  cudaStream_t st);
+size_t divmod_workspace(int64_t count, int nu, int nv);
+int launch_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count, int nv,
+                 int h, int nw, void *ws, size_t ws_bytes, cudaStream_t st);
+size_t shinv_workspace(int64_t count, int nv, int h);
+}  // namespace bigint
+
+using namespace bigint;
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char *bigint_strerror(int status) {
+  switch (status) {
+    case BIGINT_OK: return "ok";
+    case BIGINT_EINVAL: return "invalid argument";
+    case BIGINT_EDIVZERO: return "division by zero";
+    case BIGINT_ENOMEM: return "workspace too small";
+    case BIGINT_ETIMEOUT: return "device wait limit reached";
+    case BIGINT_EINTERNAL: return "internal correction limit exceeded";
+    case BIGINT_ECUDA: return "CUDA runtime error";
+    case BIGINT_ERANGE: return "quotient does not fit in the output";
+    default: return "unknown status";
+  }
+}
+
+int bigint_version(void) { return 100; }
+
+static int check_addsub(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                        int32_t n) {
+  if (count < 0 || n < 1 || n > BIGINT_MAX_LIMBS) return BIGINT_EINVAL;
+  if (count > 0 && (!a || !b || !out)) return BIGINT_EINVAL;
+  if (count > 0x7fffffff) return BIGINT_EINVAL;
+  return BIGINT_OK;
+}
+
+int bigint_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
+               int64_t count, int32_t n, void *stream) {
+  int rc = check_addsub(a, b, out, count, n);
+  if (rc != BIGINT_OK || count == 0) return rc;
+  return launch_addsub(false, a, b, out, carry_out, count, n, as_stream(stream));
+}
+
+int bigint_sub(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *borrow_out,
+               int64_t count, int32_t n, void *stream) {
+  int rc = check_addsub(a, b, out, count, n);
+  if (rc != BIGINT_OK || count == 0) return rc;
+  return launch_addsub(true, a, b, out, borrow_out, count, n, as_stream(stream));
+}
+
+int bigint_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int32_t na,
+               int32_t nb, void *stream) {
+  if (count < 0 || count > 0x7fffffff || na < 1 || nb < 1) return BIGINT_EINVAL;
+  if (na > mul_max_limbs() || nb > mul_max_limbs()) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!a || !b || !out) return BIGINT_EINVAL;
+  return launch_mul(a, b, out, count, na, nb, na + nb, as_stream(stream));
+}
+
+int bigint_mul_lo(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                  int32_t na, int32_t nb, int32_t m, void *stream) {
+  if (count < 0 || count > 0x7fffffff || na < 1 || nb < 1) return BIGINT_EINVAL;
+  if (na > mul_max_limbs() || nb > mul_max_limbs()) return BIGINT_EINVAL;
+  if (m < 1 || m > na + nb) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!a || !b || !out) return BIGINT_EINVAL;
+  return launch_mul(a, b, out, count, na, nb, m, as_stream(stream));
+}
+
+size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv) {
+  if (count < 0 || nu < 1 || nv < 1) return 0;
+  return divmod_workspace(count, nu, nv);
+}
+
+int bigint_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                  int32_t *status, int64_t count, int32_t nu, int32_t nv, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+  if (count < 0 || count > 0x7fffffff || nu < 1 || nv < 1) return BIGINT_EINVAL;
+  if (nu > BIGINT_MAX_LIMBS || nv > BIGINT_MAX_LIMBS) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!u || !v || !q || !r) return BIGINT_EINVAL;
+  if (workspace_bytes < divmod_workspace(count, nu, nv)) return BIGINT_ENOMEM;
+  if (workspace_bytes > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0))
+    return BIGINT_EINVAL;
+  return launch_divmod(u, v, q, r, status, count, nu, nv, workspace, workspace_bytes,
+                       as_stream(stream));
+}
+
+size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h) {
+  if (count < 0 || nv < 1 || h < 1) return 0;
+  return shinv_workspace(count, nv, h);
+}
+
+int bigint_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count, int32_t nv,
+                 int32_t h, int32_t nw, void *workspace, size_t workspace_bytes,
+                 void *stream) {
+  if (count < 0 || count > 0x7fffffff || nv < 1 || nw < 1) return BIGINT_EINVAL;
+  if (nv > BIGINT_MAX_LIMBS || h < nv || h > 2 * BIGINT_MAX_LIMBS) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!v || !w) return BIGINT_EINVAL;
+  if (workspace_bytes < shinv_workspace(count, nv, h)) return BIGINT_ENOMEM;
+  if (workspace_bytes > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0))
+    return BIGINT_EINVAL;
+  return launch_shinv(v, w, status, count, nv, h, nw, workspace, workspace_bytes,
+                      as_stream(stream));
+}
+
+int bigint_set_variant(int op, int variant) {
+  if (op == 0) return mul_set_variant(variant);
+  return BIGINT_EINVAL;
+}
+
+int bigint_probe_int_throughput(int variant, double *ops_per_clk_sm, double *sm_mhz) {
+  if (!ops_per_clk_sm || !sm_mhz) return BIGINT_EINVAL;
+  return probe_int_throughput(variant, ops_per_clk_sm, sm_mhz);
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// mul.cu -- batched multiplication kernels (Sec. V-B, Fig. 5).
+//
+// One CTA per instance; the whole product is computed by blk_mul
+// (mulcore.cuh) with both operands resident in shared memory.  The digit
+// size RB, the chunk width Q and the flush interval F are compile-time; a
+// few variants are instantiated and one is chosen per call (the default, or
+// the one the tuning hook selected).
+#include "mulcore.cuh"
+
+namespace bigint {
+
+template <int RB, int Q, int F>
+__global__ void __launch_bounds__(Q >= 16 ? 512 : 1024)
+    k_mul(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
+          uint64_t *__restrict__ Out, int na, int nb, int nout) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int64_t inst = blockIdx.x;
+  blk_mul<RB, Q, F>(A + inst * (int64_t)na, na, Bm + inst * (int64_t)nb, nb,
+                    Out + inst * (int64_t)nout, nout, smem);
+}
+
+// Threads per CTA for a product with `units` units of work: as few rounds as
+// the 1024-thread limit allows, then the smallest multiple of 32 that covers
+// the units in that many rounds.
+static int pick_threads(int units, int max_threads) {
+  int rounds = (units + max_threads - 1) / max_threads;
+  if (rounds < 1) rounds = 1;
+  int T = (units + rounds - 1) / rounds;
+  T = (T + 31) / 32 * 32;
+  return T < 32 ? 32 : T;
+}
+
+static int g_smem_optin = 0;
+
+static int smem_optin() {
+  if (g_smem_optin == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return 0;
+  }
+  return g_smem_optin;
+}
+
+template <int RB, int Q, int F>
+static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                          int na, int nb, int nout, cudaStream_t st) {
+  const size_t smem = sizeof(uint32_t) * (size_t)blk_mul_smem_words<RB, Q>(na, nb);
+  const int optin = smem_optin();
+  if (optin == 0) return BIGINT_ECUDA;
+  if (smem > (size_t)optin) return BIGINT_EINVAL;
+  static bool configured = false;
+  if (!configured) {
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    configured = true;
+  }
+  const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 512 : 1024);
+  k_mul<RB, Q, F><<<(unsigned)count, T, smem, st>>>(a, b, out, na, nb, nout);
+  return bigint_launch_status();
+}
+
+// Variant table: 0 = default.
+static int g_mul_variant = 0;
+
+int mul_set_variant(int v) {
+  if (v < 0 || v > 3) return BIGINT_EINVAL;
+  g_mul_variant = v;
+  return BIGINT_OK;
+}
+
+// Largest square operand (limbs) whose product fits one CTA's shared memory.
+int mul_max_limbs() { return BIGINT_MUL_MAX_LIMBS; }
+
+int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+               int nb, int nout, cudaStream_t st) {
+  switch (g_mul_variant) {
+    case 1: return launch_variant<28, 16, 128>(a, b, out, count, na, nb, nout, st);
+    case 2: return launch_variant<29, 8, 32>(a, b, out, count, na, nb, nout, st);
+    case 3: return launch_variant<30, 8, 8>(a, b, out, count, na, nb, nout, st);
+    default: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
+  }
+}
+
+}  // namespace bigint

@@ -1,0 +1,226 @@
+// mulcore.cuh -- block-level product of two limb arrays (Sec. V-B, Fig. 5).
+//
+// blk_mul<RB, Q, F>(x, nx, y, ny, out, nout, smem) writes the low nout limbs
+// of x*y to out (nout = nx + ny gives the full product).  All threads of the
+// CTA take part.
+//
+// Digits.  The operands are re-cut into digits of RB < 32 bits (one digit
+// per 32-bit word in shared memory).  A digit product then has 2*RB bits and
+// one 32x32->64-bit multiply-add (IMAD.WIDE) accumulates it into a 64-bit
+// column accumulator with no carry handling: 2^(64-2RB) products fit before
+// the accumulator can overflow.  The carries are deferred: every F row steps
+// each accumulator keeps its low RB bits and hands the rest to the next
+// column.  This replaces the paper's oneConvMul (a 128-bit product added
+// into a (low, high, carry) column triple, Sec. V-B) by one instruction per
+// digit product, the cheapest integer multiply form on sm_103a.
+//
+// Schedule.  The shorter operand is the "row" operand (one digit a_i per
+// row step, the same for every lane of a warp), the longer one the "window"
+// operand (each thread keeps 2Q consecutive digits of it in registers and
+// slides the window down one digit per step).  The columns are cut into
+// chunks of Q; a thread owns one unit of work at a time:
+//   * unit u < K_R: the balanced pair of chunk u (rising part of the column
+//     profile) and chunk K_W + u (falling part), as in Fig. 5 threadConv --
+//     their row counts (u+1)Q and (K_R-u)Q add up to (K_R+1)Q;
+//   * unit u >= K_R: one chunk of the flat middle part, K_R Q rows (+Q
+//     zero rows to keep every unit at exactly K_R+1 groups of Q steps).
+// Zero padding of Q digits on both sides of the window operand (and after
+// the row operand) lets the triangular ends of the chunks (Fig. 5 halfConv's
+// second loop) run through the same code.
+//
+// Combine (Fig. 5 combineQ / manifestShm / bmulReg).  A finished chunk is Q
+// normalised digits plus an overflow word X (the chunk's value above its Q
+// digits).  The digits are packed into their bit positions of the output
+// (limbs shared by two chunks are completed with atomicOr); the overflow
+// words go to shared memory ("Hsh").  One block-wide carry-scan addition of
+// the output and the overflow words finishes the product.
+#pragma once
+#include "blockops.cuh"
+#include "common.cuh"
+
+namespace bigint {
+
+template <int RB>
+struct Digits {
+  static constexpr uint32_t MASK = (1u << RB) - 1u;
+  // number of RB-bit digits of an n-limb number
+  static __host__ __device__ constexpr int count(int nlimbs) { return (64 * nlimbs + RB - 1) / RB; }
+  // digit k: bits [RB k, RB k + RB) of the limb array (read as 32-bit words)
+  static __device__ __forceinline__ uint32_t get(const uint32_t *w, int nwords, int k) {
+    const int bit = RB * k;
+    const int i = bit >> 5, s = bit & 31;
+    const uint32_t lo = i < nwords ? w[i] : 0u;
+    const uint32_t hi = i + 1 < nwords ? w[i + 1] : 0u;
+    return __funnelshift_r(lo, hi, s) & MASK;
+  }
+};
+
+// Shared-memory words blk_mul needs for an nx-by-ny product.
+template <int RB, int Q>
+__host__ __device__ constexpr int blk_mul_smem_words(int nx, int ny) {
+  const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
+  const int NR = NX < NY ? NX : NY, NW = NX < NY ? NY : NX;
+  const int KR = (NR + Q - 1) / Q, KW = (NW + Q - 1) / Q;
+  // row [KR Q + Q] | window [-Q, KW Q + Q) | H (64-bit) [KW + KR] | scratch
+  return (KR * Q + Q) + (KW * Q + 2 * Q) + 2 * (KW + KR) + BLK_SCRATCH_WORDS;
+}
+
+// Units of work (threads x rounds) for an nx-by-ny product.
+template <int RB, int Q>
+__host__ __device__ constexpr int blk_mul_units(int nx, int ny) {
+  const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
+  const int NW = NX < NY ? NY : NX;
+  return (NW + Q - 1) / Q;
+}
+
+template <int RB, int Q>
+__device__ __forceinline__ void normalise(uint64_t (&acc)[Q], uint64_t &X) {
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint64_t c = acc[q] >> RB;
+    acc[q] &= Digits<RB>::MASK;
+    if (q + 1 < Q) acc[q + 1] += c; else X += c;
+  }
+}
+
+// Normalise, pack the Q digits of chunk c into the output bits
+// [RB Q c, RB Q (c+1)) (limbs < nout), and park the overflow X in sH[c].
+template <int RB, int Q>
+__device__ __forceinline__ void finish_chunk(uint64_t (&acc)[Q], uint64_t X, int c,
+                                             uint64_t *out, int nout, uint64_t *sH) {
+  normalise<RB, Q>(acc, X);
+  sH[c] = X;
+  const int o = RB * Q * c;
+  int limb = o >> 6, pos = o & 63;
+  uint64_t cur = 0;
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint64_t d = acc[q];
+    cur |= d << pos;
+    pos += RB;
+    if (pos >= 64) {
+      if (limb < nout && cur) atomicOr(reinterpret_cast<unsigned long long *>(out + limb), cur);
+      limb++;
+      pos -= 64;
+      cur = pos > 0 ? d >> (RB - pos) : 0;
+    }
+  }
+  if (pos > 0 && limb < nout && cur)
+    atomicOr(reinterpret_cast<unsigned long long *>(out + limb), cur);
+}
+
+template <int Q, int T0, int RB>
+__device__ __forceinline__ void row_steps(uint64_t (&acc)[Q], const uint32_t (&W)[2 * Q],
+                                          const uint32_t *a) {
+  if constexpr (T0 < Q) {
+    const uint4 av = *reinterpret_cast<const uint4 *>(a + T0);
+    const uint32_t a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+#pragma unroll
+      for (int q = 0; q < Q; q++)  // one IMAD.WIDE.U32 per digit product
+        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a4[t]), "r"(W[Q - (T0 + t) + q]));
+    }
+    row_steps<Q, T0 + 4, RB>(acc, W, a);
+  }
+}
+
+template <int RB, int Q, int F>
+__device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t *sRow,
+                                          const uint32_t *sW, uint64_t *out, int nout,
+                                          uint64_t *sH) {
+  static_assert(F % Q == 0, "flush interval must be a whole number of groups");
+  // F digit products of 2RB bits, plus a normalised digit and an incoming
+  // carry, must fit the 64-bit accumulator
+  static_assert(F < (1 << (64 - 2 * RB)), "flush interval too long for this digit size");
+  constexpr int FG = F / Q;
+  const int NWp = KW * Q;
+  const bool pair = u < KR;
+  const int switch_g = pair ? u + 1 : -1;
+  uint64_t acc[Q], X = 0;
+  uint32_t W[2 * Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) acc[q] = 0;
+#pragma unroll
+  for (int q = 0; q < Q; q += 4) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(sW + u * Q + q);
+    W[Q + q] = v.x; W[Q + q + 1] = v.y; W[Q + q + 2] = v.z; W[Q + q + 3] = v.w;
+  }
+  bool fwd = true;
+#pragma unroll 1
+  for (int g = 0; g <= KR; g++) {
+    if (g == switch_g) {  // low chunk done: continue with its partner
+      finish_chunk<RB, Q>(acc, X, u, out, nout, sH);
+#pragma unroll
+      for (int q = 0; q < Q; q++) { acc[q] = 0; W[Q + q] = 0; }  // window[NWp..) is padding
+      X = 0;
+      fwd = false;
+    }
+    const int base = fwd ? (u - g) * Q : NWp + (u + 1 - g) * Q;
+    const int i0 = fwd ? g * Q : (g - 1) * Q;
+#pragma unroll
+    for (int q = 0; q < Q; q += 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(sW + base - Q + q);
+      W[q] = v.x; W[q + 1] = v.y; W[q + 2] = v.z; W[q + 3] = v.w;
+    }
+    row_steps<Q, 0, RB>(acc, W, sRow + i0);
+#pragma unroll
+    for (int q = 0; q < Q; q++) W[Q + q] = W[q];
+    if ((g + 1) % FG == 0) normalise<RB, Q>(acc, X);
+  }
+  finish_chunk<RB, Q>(acc, X, pair ? KW + u : u, out, nout, sH);
+}
+
+// Low nout limbs of x[0..nx) * y[0..ny) into out[0..nout) (out must not
+// overlap x or y).  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
+// aligned.  Returns the carry out of limb nout-1 of the final addition
+// (0 whenever nout >= nx + ny).
+template <int RB, int Q, int F>
+__device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
+                            int nout, uint32_t *smem) {
+  const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
+  const bool x_is_row = NX <= NY;
+  const uint32_t *rw = reinterpret_cast<const uint32_t *>(x_is_row ? x : y);
+  const uint32_t *ww = reinterpret_cast<const uint32_t *>(x_is_row ? y : x);
+  const int NR = x_is_row ? NX : NY, NW = x_is_row ? NY : NX;
+  const int rwords = 2 * (x_is_row ? nx : ny), wwords = 2 * (x_is_row ? ny : nx);
+  const int KR = (NR + Q - 1) / Q, KW = (NW + Q - 1) / Q;
+  // Every region starts on a multiple of Q >= 4 words: 16-byte aligned.
+  uint32_t *sRow = smem;                                             // [KR Q + Q]
+  uint32_t *sW = smem + (KR * Q + Q) + Q;                            // [-Q, KW Q + Q)
+  uint64_t *sH = reinterpret_cast<uint64_t *>(sW + KW * Q + Q);      // [KW + KR]
+  uint32_t *scr = reinterpret_cast<uint32_t *>(sH + (KW + KR));      // scratch
+  const int T = blockDim.x, t = threadIdx.x;
+
+  // ---- A1: stage both operands as RB-bit digits, zero padded; clear out
+  for (int k = t; k < KR * Q + Q; k += T) sRow[k] = k < NR ? Digits<RB>::get(rw, rwords, k) : 0u;
+  for (int k = t - Q; k < KW * Q + Q; k += T) sW[k] = (k >= 0 && k < NW) ? Digits<RB>::get(ww, wwords, k) : 0u;
+  for (int j = t; j < nout; j += T) out[j] = 0;
+  __syncthreads();
+
+  // ---- A3: convolution, one unit at a time per thread
+  for (int u = t; u < KW; u += T) conv_unit<RB, Q, F>(u, KR, KW, sRow, sW, out, nout, sH);
+  __syncthreads();
+
+  // ---- A4: out += overflow words, one carry-scan addition
+  const int CB = RB * Q;  // bits per chunk
+  const int nch = KW + KR;
+  auto load = [&](int j) -> ulonglong2 {
+    const int c1 = (64 * j) / CB - 1;  // last chunk whose overflow starts at or below bit 64j
+    uint64_t add = 0;
+    if (c1 >= 0 && c1 < nch) {
+      const int d = 64 * j - CB * (c1 + 1);
+      if (d < 64) add |= sH[c1] >> d;
+    }
+    const int c2 = c1 + 1;
+    if (c2 >= 0 && c2 < nch) {
+      const int o2 = CB * (c2 + 1) - 64 * j;  // > 0
+      if (o2 < 64) add |= sH[c2] << o2;
+    }
+    return make_ulonglong2(out[j], add);
+  };
+  auto store = [&](int j, uint64_t v) { out[j] = v; };
+  return blk_addsub<false>(nout, 0u, load, store, scr);
+}
+
+}  // namespace bigint

@@ -147,3 +147,56 @@ def ragged_sizes(seed: int, count: int, lo_bits: int = 15, hi_bits: int = 19,
     bits = np.power(2.0, lo_bits + (hi_bits - lo_bits) * u01)
     n = np.rint(bits / 64.0).astype(np.int64)
     return np.clip(n, min_limbs, max_limbs)
+
+
+# ---------------------------------------------------------------------------
+# The same generator evaluated with torch on a device (for the large bench
+# arrays); bit-identical to the numpy version above.
+# ---------------------------------------------------------------------------
+def _s64(x: int) -> int:
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def uniform_torch(seed: int, count: int, device="cuda", start: int = 0):
+    """Same values as uniform(seed, count, start), as an int64 tensor."""
+    import torch
+
+    def lsr(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    gamma = _s64(int(GAMMA))
+    m1, m2 = _s64(int(_M1)), _s64(int(_M2))
+    base = _s64(seed * (1 << 32))
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    chunk = 1 << 24
+    for s in range(0, count, chunk):
+        e = min(count, s + chunk)
+        z = torch.arange(start + s + 1, start + e + 1, dtype=torch.int64, device=device)
+        z = base + z * gamma
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        out[s:e] = z ^ lsr(z, 31)
+    return out
+
+
+def limbs_torch(seed: int, count: int, n: int, top_nonzero: bool = False, device="cuda"):
+    """Same values as limbs(...), as a (count, n) int64 tensor on `device`."""
+    x = uniform_torch(seed, count * n, device).view(count, n)
+    if top_nonzero and n > 0:
+        k = 0
+        while True:
+            z = (x[:, -1] == 0).nonzero().flatten()
+            if z.numel() == 0:
+                break
+            x[z, -1] = uniform_torch(seed + 7919 + k, z.numel(), device)
+            k += 1
+    return x
+
+
+def config_sweep_torch(n: int, seed: int = 2, batch: int | None = None, device="cuda"):
+    if batch is None:
+        batch = (1 << 26) // n
+    a = limbs_torch(seed * 100 + n, batch, n, True, device)
+    b = limbs_torch(seed * 100 + n + 50, batch, n, True, device)
+    return a, b
