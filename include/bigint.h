@@ -126,10 +126,13 @@ size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h);
 /* ---- tuning and measurement ---------------------------------------------
  * Selects the kernel variant an operation uses from now on (process-wide,
  * not thread-safe; call it before launching work).  op 0 = multiply:
- *   variant 0 (default): 28-bit digits, 8-column chunks, carries every 128 rows
- *   variant 1: 28-bit digits, 16-column chunks, carries every 128 rows
+ *   variant 0 (default): chosen by operand size from GB300 measurements
+ *   variant 1: 28-bit digits, 8-column chunks, carries every 128 rows
  *   variant 2: 29-bit digits, 8-column chunks, carries every 32 rows
- *   variant 3: 30-bit digits, 8-column chunks, carries every 8 rows
+ *   variant 3: 29-bit digits, 4-column chunks, carries every 32 rows
+ *   variant 4: 29-bit digits, 16-column chunks, carries every 32 rows
+ *   variant 5: 30-bit digits, 8-column chunks, carries every 8 rows
+ *   variant 6: as 2, each digit product written as explicit mad.wide.u32
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 

@@ -43,8 +43,13 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB_PATH)
+        # ORACLE_LIB points the pins at a deliberately broken build of this
+        # oracle (tests/test_oracle_mutants.py); normal runs never set it.
+        path = os.environ.get("ORACLE_LIB")
+        if not path:
+            build()
+            path = _LIB_PATH
+        L = ctypes.CDLL(path)
         p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         L.orc_add.argtypes = [p, p, p, i64]
         L.orc_sub.argtypes = [p, p, p, i64]

@@ -109,7 +109,10 @@ __device__ __forceinline__ void finish_chunk(uint64_t (&acc)[Q], uint64_t X, int
     atomicOr(reinterpret_cast<unsigned long long *>(out + limb), cur);
 }
 
-template <int Q, int T0, int RB>
+// ASM selects how the digit product is written: as one explicit
+// mad.wide.u32 per product, or as a C++ 64-bit multiply-add that the
+// compiler maps to IMAD.WIDE.U32 (and may schedule differently).
+template <int Q, int T0, bool ASM>
 __device__ __forceinline__ void row_steps(uint64_t (&acc)[Q], const uint32_t (&W)[2 * Q],
                                           const uint32_t *a) {
   if constexpr (T0 < Q) {
@@ -118,14 +121,18 @@ __device__ __forceinline__ void row_steps(uint64_t (&acc)[Q], const uint32_t (&W
 #pragma unroll
     for (int t = 0; t < 4; t++) {
 #pragma unroll
-      for (int q = 0; q < Q; q++)  // one IMAD.WIDE.U32 per digit product
-        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a4[t]), "r"(W[Q - (T0 + t) + q]));
+      for (int q = 0; q < Q; q++) {  // one IMAD.WIDE.U32 per digit product
+        if constexpr (ASM)
+          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a4[t]), "r"(W[Q - (T0 + t) + q]));
+        else
+          acc[q] += (uint64_t)a4[t] * (uint64_t)W[Q - (T0 + t) + q];
+      }
     }
-    row_steps<Q, T0 + 4, RB>(acc, W, a);
+    row_steps<Q, T0 + 4, ASM>(acc, W, a);
   }
 }
 
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool ASM>
 __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t *sRow,
                                           const uint32_t *sW, uint64_t *out, int nout,
                                           uint64_t *sH) {
@@ -163,7 +170,7 @@ __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t 
       const uint4 v = *reinterpret_cast<const uint4 *>(sW + base - Q + q);
       W[q] = v.x; W[q + 1] = v.y; W[q + 2] = v.z; W[q + 3] = v.w;
     }
-    row_steps<Q, 0, RB>(acc, W, sRow + i0);
+    row_steps<Q, 0, ASM>(acc, W, sRow + i0);
 #pragma unroll
     for (int q = 0; q < Q; q++) W[Q + q] = W[q];
     if ((g + 1) % FG == 0) normalise<RB, Q>(acc, X);
@@ -175,7 +182,7 @@ __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t 
 // overlap x or y).  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
 // aligned.  Returns the carry out of limb nout-1 of the final addition
 // (0 whenever nout >= nx + ny).
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool ASM = false>
 __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
                             int nout, uint32_t *smem) {
   const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
@@ -199,7 +206,7 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
   __syncthreads();
 
   // ---- A3: convolution, one unit at a time per thread
-  for (int u = t; u < KW; u += T) conv_unit<RB, Q, F>(u, KR, KW, sRow, sW, out, nout, sH);
+  for (int u = t; u < KW; u += T) conv_unit<RB, Q, F, ASM>(u, KR, KW, sRow, sW, out, nout, sH);
   __syncthreads();
 
   // ---- A4: out += overflow words, one carry-scan addition

@@ -78,74 +78,38 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
     }
 #pragma unroll
     for (int q = 0; q < 8; q++) y[q] += acc[q];
-  } else if constexpr (VARIANT == 5) {
-    // as 3 with 16 accumulators and a 32-digit window
-    uint64_t acc[16];
-    uint32_t W[32];
+  } else if constexpr (VARIANT == 5 || VARIANT == 6) {
+    // as 3 with the window digit as the first multiplicand and the row
+    // digit second; 5: 8 accumulators, 6: 16 accumulators
+    constexpr int QQ = VARIANT == 5 ? 8 : 16;
+    uint64_t acc[QQ];
+    uint32_t W[2 * QQ];
 #pragma unroll
-    for (int q = 0; q < 16; q++) acc[q] = x[q & 7];
+    for (int q = 0; q < QQ; q++) acc[q] = x[q & 7];
 #pragma unroll
-    for (int q = 0; q < 32; q++) W[q] = x[(q + 3) & 7] + q;
+    for (int q = 0; q < 2 * QQ; q++) W[q] = x[(q + 3) & 7] + q;
 #pragma unroll 1
     for (int it = 0; it < PROBE_ITERS / 8; it++) {
 #pragma unroll
       for (int t = 0; t < 8; t++) {
         const uint32_t a = x[t] ^ (uint32_t)it;
 #pragma unroll
-        for (int q = 0; q < 16; q++)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a), "r"(W[16 - t + q]));
+        for (int q = 0; q < QQ; q++)
+          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(W[QQ - t + q]), "r"(a));
       }
 #pragma unroll
-      for (int q = 0; q < 16; q++) W[16 + q] = W[q] + (uint32_t)it;
+      for (int q = 0; q < QQ; q++) W[QQ + q] = W[q] + (uint32_t)it;
     }
 #pragma unroll
-    for (int q = 0; q < 16; q++) y[q & 7] += acc[q];
-  } else if constexpr (VARIANT == 6) {
-    // as 3, with the window digits and the row digits read from shared
-    // memory (16-byte aligned vector loads, largest index 267 < 288)
-    __shared__ __align__(16) uint32_t sw[288];
-    for (int i = threadIdx.x; i < 288; i += blockDim.x) sw[i] = seed * i + 1;
-    __syncthreads();
-    uint64_t acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; q++) acc[q] = x[q];
-    const uint32_t *wp = sw + (threadIdx.x & 31) * 8;
-#pragma unroll 1
-    for (int it = 0; it < PROBE_ITERS / 8; it++) {
-      uint32_t W[16];
-      const int o = (it * 4) & 7;
-      const uint4 v0 = *reinterpret_cast<const uint4 *>(wp + o);
-      const uint4 v1 = *reinterpret_cast<const uint4 *>(wp + o + 4);
-      const uint4 v2 = *reinterpret_cast<const uint4 *>(wp + 8);
-      const uint4 v3 = *reinterpret_cast<const uint4 *>(wp + 12);
-      const uint4 a0 = *reinterpret_cast<const uint4 *>(sw + 256 + o);
-      const uint4 a1 = *reinterpret_cast<const uint4 *>(sw + 260 + o);
-      W[0] = v0.x; W[1] = v0.y; W[2] = v0.z; W[3] = v0.w; W[4] = v1.x; W[5] = v1.y;
-      W[6] = v1.z; W[7] = v1.w; W[8] = v2.x; W[9] = v2.y; W[10] = v2.z; W[11] = v2.w;
-      W[12] = v3.x; W[13] = v3.y; W[14] = v3.z; W[15] = v3.w;
-      const uint32_t av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-      for (int t = 0; t < 8; t++) {
-#pragma unroll
-        for (int q = 0; q < 8; q++)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(av[t]), "r"(W[8 - t + q]));
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; q++) y[q] += acc[q];
+    for (int q = 0; q < QQ; q++) y[q & 7] += acc[q];
   } else {
-    // 32-bit multiply-add (low half) into 16 independent chains
-    uint32_t z[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) z[k] = x[k & 7] + k;
+    // as 0 with the operands swapped (constant first, varying second)
 #pragma unroll 1
-    for (int it = 0; it < PROBE_ITERS / 2; it++) {
+    for (int it = 0; it < PROBE_ITERS; it++) {
 #pragma unroll
-      for (int k = 0; k < 16; k++)
-        asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(z[k]) : "r"(m), "r"(m));
+      for (int k = 0; k < 8; k++)
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(m), "r"(x[k]));
     }
-#pragma unroll
-    for (int k = 0; k < 16; k++) x[k & 7] += z[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) cycles[blockIdx.x] = clock64() - t0;
@@ -157,9 +121,8 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 
 // Operations per thread for one probe launch.
 static double probe_ops_per_thread(int variant) {
-  if (variant == 3 || variant == 4 || variant == 6) return (double)(PROBE_ITERS / 8) * 64;
-  if (variant == 5) return (double)(PROBE_ITERS / 8) * 128;
-  if (variant == 7) return (double)(PROBE_ITERS / 2) * 16;
+  if (variant == 3 || variant == 4 || variant == 5) return (double)(PROBE_ITERS / 8) * 64;
+  if (variant == 6) return (double)(PROBE_ITERS / 8) * 128;
   return (double)PROBE_ITERS * 8;
 }
 
