@@ -74,10 +74,11 @@ int bigint_sub(const uint64_t *a, const uint64_t *b, uint64_t *out,
 
 /* ---- multiplication (Sec. V-B, Fig. 5) ----------------------------------
  * out = a * b, the FULL product of na + nb limbs per instance.  The
- * convolution C_k = sum_{i+j=k} a_i b_j is computed column-block by
- * column-block with a balanced assignment of column blocks to threads
- * (Fig. 5 threadConv), each block accumulated as (Q digits, high, carry)
- * (Fig. 5 combineQ); the per-block overflow words are then added in by one
+ * convolution C_k = sum_{i+j=k} a_i b_j (Sec. V-B) is computed by column
+ * blocks ("chunks") with a balanced assignment of chunks to threads (Fig. 5
+ * threadConv: a rising chunk paired with a falling one), each digit product
+ * accumulated by one 32x32->64-bit multiply-add with deferred carries; each
+ * chunk's digits and overflow word (Fig. 5 combineQ) are finished by one
  * carry-scan addition (Fig. 5 bmulReg).
  * a: count*na limbs, b: count*nb limbs, out: count*(na+nb) limbs.
  * 1 <= na, nb <= BIGINT_MUL_MAX_LIMBS.                                     */
@@ -123,6 +124,75 @@ int bigint_shinv(const uint64_t *v, uint64_t *w, int32_t *status,
                  void *workspace, size_t workspace_bytes, void *stream);
 size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h);
 
+/* ---- ragged batches of mixed operations (the batched form) --------------
+ * A batch is an array of operation descriptors over one input pool and one
+ * output pool of limbs (device memory, caller-owned).  Offsets are in limbs
+ * from the start of the pool.  Each operation is exactly the uniform entry
+ * point's computation (same kernels' block routines), so results do not
+ * depend on the batch an operation runs in.
+ *   ADD/SUB: out[o1 .. o1+na) = a +- b (na == nb); status = carry / borrow
+ *   MUL:     out[o1 .. o1+na+nb) = a * b (na, nb <= BIGINT_MUL_MAX_LIMBS)
+ *   DIVMOD:  u = a (na limbs), v = b (nb limbs); q at o1 (max(na-nb+1,1)
+ *            limbs), r at o2 (nb limbs); status as for bigint_divmod.
+ * Output ranges must not overlap each other or the inputs.               */
+#define BIGINT_OP_ADD 1
+#define BIGINT_OP_SUB 2
+#define BIGINT_OP_MUL 3
+#define BIGINT_OP_DIVMOD 4
+typedef struct {
+  int32_t op;        /* BIGINT_OP_*                                       */
+  int32_t na, nb;    /* limbs of a and b                                  */
+  int32_t reserved;  /* 0                                                 */
+  int64_t a, b;      /* input offsets (limbs)                             */
+  int64_t o1, o2;    /* output offsets (limbs)                            */
+} bigint_op;
+
+/* Launch forms: one persistent launch with a device-side work queue
+ * (cost-sorted, largest first), or one launch per (op, size class). */
+#define BIGINT_BATCH_PERSISTENT 0
+#define BIGINT_BATCH_PER_CLASS 1
+
+typedef struct bigint_batch bigint_batch; /* opaque host-side plan */
+
+/* Validates the host array of descriptors, sorts and groups it, and picks
+ * the launch shapes.  Host memory only; the descriptors are copied.
+ * Returns BIGINT_EINVAL for a malformed descriptor. */
+int bigint_batch_create(const bigint_op *ops_host, int64_t nops,
+                        bigint_batch **batch);
+/* Device workspace bytes the batch needs (descriptors, queue, division
+ * scratch for each resident CTA). */
+size_t bigint_batch_workspace(const bigint_batch *batch);
+/* Copies the plan into the workspace (asynchronous on `stream`; the host
+ * copy stays owned by the batch until bigint_batch_destroy). */
+int bigint_batch_upload(bigint_batch *batch, void *workspace, size_t bytes,
+                        void *stream);
+/* Runs the batch (device work only: a counter reset and one kernel, or one
+ * kernel per class), so it can be captured in a CUDA graph.  status: one
+ * int32 per operation, or NULL. */
+int bigint_batch_launch(const bigint_batch *batch, const uint64_t *in_pool,
+                        uint64_t *out_pool, int32_t *status, void *workspace,
+                        int mode, void *stream);
+/* Autotuner: times the persistent form with each candidate CTA size on this
+ * batch (synchronous) and keeps the fastest for this batch and as the
+ * process default; *best_threads receives it. */
+int bigint_batch_tune(bigint_batch *batch, const uint64_t *in_pool,
+                      uint64_t *out_pool, int32_t *status, void *workspace,
+                      size_t bytes, void *stream, int *best_threads);
+void bigint_batch_destroy(bigint_batch *batch);
+
+/* Autotuner for the uniform multiply: times the variants of
+ * bigint_set_variant on this batch (synchronous), records the fastest for
+ * the operands' size class (used by variant 0 from then on) and returns it
+ * in *best_variant. */
+int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
+                    int64_t count, int32_t na, int32_t nb, void *stream,
+                    int *best_variant);
+/* Saves / loads the tuning table (multiply variant per size class, batch
+ * CTA size) as a small JSON file keyed by the GPU name.  Loading a table
+ * written for another GPU returns BIGINT_EINVAL and changes nothing. */
+int bigint_tuning_save(const char *path);
+int bigint_tuning_load(const char *path);
+
 /* ---- tuning and measurement ---------------------------------------------
  * Selects the kernel variant an operation uses from now on (process-wide,
  * not thread-safe; call it before launching work).  op 0 = multiply:
@@ -133,6 +203,8 @@ size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h);
  *   variant 4: 29-bit digits, 16-column chunks, carries every 32 rows
  *   variant 5: 30-bit digits, 8-column chunks, carries every 8 rows
  *   variant 6: as 2, each digit product written as explicit mad.wide.u32
+ *   variants 7, 8, 9: as 1 with 16-column chunks, as 4, as 1 -- with the
+ *   sliding window held in two alternating register buffers (no moves)
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 

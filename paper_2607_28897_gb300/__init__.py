@@ -22,6 +22,8 @@ __all__ = [
 ]
 
 OK, EINVAL, EDIVZERO, ENOMEM, ETIMEOUT, EINTERNAL, ECUDA, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
+OP_ADD, OP_SUB, OP_MUL, OP_DIVMOD = 1, 2, 3, 4
+BATCH_PERSISTENT, BATCH_PER_CLASS = 0, 1
 MAX_LIMBS = 16384
 MUL_MAX_LIMBS = 10000
 
@@ -41,6 +43,17 @@ SIGNATURES = {
     "bigint_divmod_workspace": ([_I64, _I32, _I32], _SZ),
     "bigint_shinv": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_shinv_workspace": ([_I64, _I32, _I32], _SZ),
+    "bigint_batch_create": ([_P, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "bigint_batch_workspace": ([_P], _SZ),
+    "bigint_batch_upload": ([_P, _P, _SZ, _P], ctypes.c_int),
+    "bigint_batch_launch": ([_P, _P, _P, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "bigint_batch_tune": ([_P, _P, _P, _P, _P, _SZ, _P, ctypes.POINTER(ctypes.c_int)],
+                          ctypes.c_int),
+    "bigint_batch_destroy": ([_P], None),
+    "bigint_tune_mul": ([_P, _P, _P, _I64, _I32, _I32, _P, ctypes.POINTER(ctypes.c_int)],
+                        ctypes.c_int),
+    "bigint_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
+    "bigint_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -233,3 +246,82 @@ def probe_int_throughput(variant: int):
     rc = load().bigint_probe_int_throughput(variant, ctypes.byref(ops), ctypes.byref(mhz))
     _check(rc, "bigint_probe_int_throughput")
     return ops.value, mhz.value
+
+
+# ---- ragged batches -------------------------------------------------------
+def op_dtype():
+    """numpy dtype of one bigint_op descriptor (include/bigint.h)."""
+    import numpy as np
+
+    return np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("reserved", "<i4"),
+                     ("a", "<i8"), ("b", "<i8"), ("o1", "<i8"), ("o2", "<i8")])
+
+
+class Batch:
+    """A ragged batch of mixed operations over an input and an output pool.
+
+    ``ops`` is a numpy array of ``op_dtype()``; offsets are in limbs.  The
+    plan (sort, size classes, launch shapes) is built on the host by the C
+    library; ``launch`` only enqueues device work, so it can be captured in
+    a CUDA graph."""
+
+    def __init__(self, ops, device="cuda", stream=None):
+        import numpy as np
+        import torch
+
+        self.ops = np.ascontiguousarray(ops, dtype=op_dtype())
+        h = ctypes.c_void_p()
+        _check(load().bigint_batch_create(self.ops.ctypes.data, len(self.ops), ctypes.byref(h)),
+               "bigint_batch_create")
+        self._h = h
+        self.workspace_bytes = int(load().bigint_batch_workspace(h))
+        self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                     device=device)
+        _check(load().bigint_batch_upload(h, self.workspace.data_ptr(), self.workspace.numel(),
+                                          _stream_ptr(stream)), "bigint_batch_upload")
+
+    def launch(self, in_pool, out_pool, status=None, mode=BATCH_PERSISTENT, stream=None):
+        rc = load().bigint_batch_launch(self._h, in_pool.data_ptr(), out_pool.data_ptr(),
+                                        status.data_ptr() if status is not None else None,
+                                        self.workspace.data_ptr(), mode, _stream_ptr(stream))
+        _check(rc, "bigint_batch_launch")
+
+    def tune(self, in_pool, out_pool, status=None, stream=None) -> int:
+        best = ctypes.c_int()
+        rc = load().bigint_batch_tune(self._h, in_pool.data_ptr(), out_pool.data_ptr(),
+                                      status.data_ptr() if status is not None else None,
+                                      self.workspace.data_ptr(), self.workspace.numel(),
+                                      _stream_ptr(stream), ctypes.byref(best))
+        _check(rc, "bigint_batch_tune")
+        return best.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bigint_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune_mul(a, b, out=None, stream=None) -> int:
+    """Times the multiply variants on this batch; records and returns the best."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, na = a.shape
+    nb = b.shape[1]
+    out = _empty_like_limbs(a, count, na + nb) if out is None else out
+    best = ctypes.c_int()
+    _check(load().bigint_tune_mul(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
+                                  _stream_ptr(stream), ctypes.byref(best)), "bigint_tune_mul")
+    return best.value
+
+
+def tuning_save(path: str) -> None:
+    _check(load().bigint_tuning_save(path.encode()), "bigint_tuning_save")
+
+
+def tuning_load(path: str) -> None:
+    _check(load().bigint_tuning_load(path.encode()), "bigint_tuning_load")

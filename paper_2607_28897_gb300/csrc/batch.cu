@@ -1,0 +1,345 @@
+// batch.cu -- ragged batches of mixed operations (add, sub, mul, divmod).
+//
+// A batch is a list of operation descriptors (bigint_op, include/bigint.h)
+// over one input pool and one output pool of limbs.  Two ways to run it:
+//
+//   * persistent: ONE launch of grid = SMs x resident CTAs; every CTA takes
+//     the next operation from a device-side work queue (one atomicAdd on a
+//     counter per operation) until the queue is empty.  The queue order is
+//     the operations sorted by estimated cost, largest first, so the tail of
+//     the launch is made of small operations.  The launch (counter reset +
+//     kernel) contains no host-side step and can be captured in a CUDA graph.
+//   * per class: one launch per (operation, size class) with size classes
+//     [2^k, 2^(k+1)) limbs, each launch striding over its class -- the
+//     plain form the persistent one is compared against.
+//
+// Each operation is executed by the whole CTA with the block-level routines
+// of the uniform kernels (blk_addsub, blk_mul, divc::divmod_one), so a
+// result is bit-identical whichever form, CTA size or batch it runs in.
+// Workspace: the division scratch of one operation per CTA.
+#include <algorithm>
+#include <vector>
+
+#include "divcore.cuh"
+
+namespace bigint {
+
+using namespace divc;
+
+struct OpDev {
+  int32_t op, na, nb, pad;
+  int64_t a, b, o1, o2;
+};
+static_assert(sizeof(OpDev) == sizeof(bigint_op), "descriptor layout");
+
+// Product variant used by batch kernels (both operands in shared memory).
+constexpr int BRB = 28, BQ = 8, BF = 128;
+constexpr int BATCH_MAX_THREADS = 640;
+
+__device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uint64_t *out,
+                                         uint64_t *ws, uint32_t *smem, int smem_words,
+                                         uint32_t *scr) {
+  switch (o.op) {
+    case BIGINT_OP_ADD:
+    case BIGINT_OP_SUB: {
+      const uint64_t *a = in + o.a, *b = in + o.b;
+      uint64_t *r = out + o.o1;
+      auto load = [&](int j) { return make_ulonglong2(a[j], b[j]); };
+      auto store = [&](int j, uint64_t x) { r[j] = x; };
+      return o.op == BIGINT_OP_ADD ? (int)blk_addsub<false>(o.na, 0u, load, store, scr)
+                                   : (int)blk_addsub<true>(o.na, 0u, load, store, scr);
+    }
+    case BIGINT_OP_MUL:
+      blk_mul<BRB, BQ, BF>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, o.na + o.nb, smem);
+      return 0;
+    case BIGINT_OP_DIVMOD: {
+      const int nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
+      return divmod_one(in + o.a, o.na, in + o.b, o.nb, out + o.o1, nq, out + o.o2, ws, smem,
+                        smem_words, scr);
+    }
+    default:
+      return BIGINT_EINVAL;
+  }
+}
+
+__global__ void __launch_bounds__(BATCH_MAX_THREADS)
+    k_batch(const OpDev *__restrict__ ops, const int32_t *__restrict__ order, int first,
+            int count, const uint64_t *in, uint64_t *out, int32_t *status, uint64_t *ws,
+            int64_t ws_per_cta, int *queue, int smem_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  __shared__ int s_idx;
+  uint64_t *my_ws = ws + (int64_t)blockIdx.x * ws_per_cta;
+  int stride_idx = blockIdx.x;
+  for (;;) {
+    int idx;
+    if (queue != nullptr) {  // persistent: take the next operation
+      if (threadIdx.x == 0) s_idx = atomicAdd(queue, 1);
+      __syncthreads();
+      idx = s_idx;
+      __syncthreads();
+    } else {  // per class: static stride over the class
+      idx = stride_idx;
+      stride_idx += gridDim.x;
+    }
+    if (idx >= count) break;
+    const int opi = order[first + idx];
+    const OpDev o = ops[opi];
+    const int st = op_status(o, in, out, my_ws, smem, smem_words, scr);
+    if (status != nullptr && threadIdx.x == 0) status[opi] = st;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+double op_cost(const bigint_op &o) {
+  switch (o.op) {
+    case BIGINT_OP_ADD:
+    case BIGINT_OP_SUB: return (double)o.na;
+    case BIGINT_OP_MUL: return (double)o.na * o.nb;
+    case BIGINT_OP_DIVMOD: {
+      const double nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
+      return 2.0 * nq * o.nb + 1.4 * (double)o.nb * std::min<double>(o.nb, nq) + o.na;
+    }
+    default: return 0;
+  }
+}
+
+int size_class(const bigint_op &o) {
+  const int n = o.na > o.nb ? o.na : o.nb;
+  int c = 0;
+  while ((2 << c) <= n) c++;
+  return c;
+}
+
+int op_smem_words(const bigint_op &o) {
+  if (o.op == BIGINT_OP_MUL) return blk_mul_smem_words<BRB, BQ>(o.na, o.nb);
+  if (o.op == BIGINT_OP_DIVMOD) return blk_mul_smem_words<DRB, DQ>(o.na, o.na);
+  return BLK_SCRATCH_WORDS;
+}
+
+int op_units(const bigint_op &o) {
+  const int a = std::min(o.na, 8192), b = std::min(o.nb, 8192);
+  if (o.op == BIGINT_OP_MUL) return blk_mul_units<BRB, BQ>(a, b);
+  if (o.op == BIGINT_OP_DIVMOD) return blk_mul_units<DRB, DQ>(a, a);
+  return std::min(o.na / 8 + 32, 512);
+}
+
+int threads_for_units(int units) {
+  int rounds = (units + BATCH_MAX_THREADS - 1) / BATCH_MAX_THREADS;
+  int T = (units + rounds - 1) / rounds;
+  T = (T + 31) / 32 * 32;
+  return std::max(64, std::min(T, BATCH_MAX_THREADS));
+}
+
+int g_batch_threads = 0;  // tuned CTA size of persistent launches (0: from the sizes)
+
+struct Launch {
+  int first, count, threads, ctas, smem_words;
+};
+
+}  // namespace
+
+int batch_set_threads(int t) {
+  if (t != 0 && (t < 64 || t > BATCH_MAX_THREADS || t % 32)) return BIGINT_EINVAL;
+  g_batch_threads = t;
+  return BIGINT_OK;
+}
+int batch_get_threads() { return g_batch_threads; }
+
+}  // namespace bigint
+
+// The opaque batch handle of include/bigint.h.
+struct bigint_batch {
+  std::vector<bigint_op> ops;
+  std::vector<int32_t> order_persistent;  // cost-sorted, largest first
+  std::vector<int32_t> order_classes;     // grouped by (op, size class)
+  std::vector<bigint::Launch> classes;    // one launch per class
+  bigint::Launch persistent;
+  int64_t ws_limbs_per_cta = 0;
+  int max_ctas = 0;
+  size_t desc_off = 0, order_p_off = 0, order_c_off = 0, queue_off = 0, scratch_off = 0;
+  size_t workspace_bytes = 0;
+  int sms = 0, optin = 0;
+  int threads_override = 0;  // set by the tuner for this batch
+};
+
+namespace bigint {
+namespace {
+
+constexpr int STATIC_SMEM = BLK_SCRATCH_WORDS * 4 + 16;
+
+int occupancy(int threads, int smem_words, int *per_sm) {
+  static bool configured = false;
+  int dev = 0, optin = 0;
+  BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+  BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (!configured) {
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - STATIC_SMEM));
+    configured = true;
+  }
+  BIGINT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch, threads,
+                                                                (size_t)smem_words * 4));
+  if (*per_sm < 1) *per_sm = 1;
+  return BIGINT_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+int batch_configure(bigint_batch *B) {
+  const int64_t n = (int64_t)B->ops.size();
+  const int max_words = (B->optin - STATIC_SMEM) / 4;
+  // persistent launch: one shape for every operation
+  int words = BLK_SCRATCH_WORDS, units = 32;
+  for (const bigint_op &o : B->ops) {
+    words = std::max(words, op_smem_words(o));
+    units = std::max(units, op_units(o));
+  }
+  Launch &P = B->persistent;
+  P.first = 0;
+  P.count = (int)n;
+  P.smem_words = std::min(words, max_words);
+  P.threads = B->threads_override ? B->threads_override
+                                   : (g_batch_threads ? g_batch_threads : threads_for_units(units));
+  int per_sm = 1;
+  int rc = occupancy(P.threads, P.smem_words, &per_sm);
+  if (rc != BIGINT_OK) return rc;
+  P.ctas = B->sms * per_sm;
+  B->max_ctas = P.ctas;
+  // per-class launches
+  B->classes.clear();
+  for (size_t i = 0; i < B->order_classes.size();) {
+    const bigint_op &o0 = B->ops[B->order_classes[i]];
+    size_t j = i;
+    int w = BLK_SCRATCH_WORDS, u = 32;
+    while (j < B->order_classes.size()) {
+      const bigint_op &o = B->ops[B->order_classes[j]];
+      if (o.op != o0.op || size_class(o) != size_class(o0)) break;
+      w = std::max(w, op_smem_words(o));
+      u = std::max(u, op_units(o));
+      j++;
+    }
+    Launch L;
+    L.first = (int)i;
+    L.count = (int)(j - i);
+    L.smem_words = std::min(w, max_words);
+    L.threads = threads_for_units(u);
+    rc = occupancy(L.threads, L.smem_words, &per_sm);
+    if (rc != BIGINT_OK) return rc;
+    L.ctas = std::min(L.count, B->sms * per_sm);
+    B->max_ctas = std::max(B->max_ctas, L.ctas);
+    B->classes.push_back(L);
+    i = j;
+  }
+  // workspace: descriptors | two orders | queue counter | per-CTA scratch
+  B->desc_off = 0;
+  B->order_p_off = align256(n * sizeof(bigint_op));
+  B->order_c_off = B->order_p_off + align256(n * 4);
+  B->queue_off = B->order_c_off + align256(n * 4);
+  B->scratch_off = B->queue_off + 256;
+  B->workspace_bytes = B->scratch_off + (size_t)B->max_ctas * B->ws_limbs_per_cta * 8;
+  return BIGINT_OK;
+}
+
+int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out) {
+  if (!out || nops < 0 || nops > 0x7fffffff || (nops > 0 && !ops)) return BIGINT_EINVAL;
+  for (int64_t i = 0; i < nops; i++) {
+    const bigint_op &o = ops[i];
+    if (o.op < BIGINT_OP_ADD || o.op > BIGINT_OP_DIVMOD) return BIGINT_EINVAL;
+    if (o.na < 1 || o.nb < 1 || o.na > BIGINT_MAX_LIMBS || o.nb > BIGINT_MAX_LIMBS)
+      return BIGINT_EINVAL;
+    if ((o.op == BIGINT_OP_ADD || o.op == BIGINT_OP_SUB) && o.na != o.nb) return BIGINT_EINVAL;
+    if (o.op == BIGINT_OP_MUL && (o.na > BIGINT_MUL_MAX_LIMBS || o.nb > BIGINT_MUL_MAX_LIMBS))
+      return BIGINT_EINVAL;
+    if (o.a < 0 || o.b < 0 || o.o1 < 0 || o.o2 < 0) return BIGINT_EINVAL;
+  }
+  bigint_batch *B = new bigint_batch;
+  B->ops.assign(ops, ops + nops);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&B->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess) {
+    delete B;
+    return BIGINT_ECUDA;
+  }
+  B->order_persistent.resize(nops);
+  B->order_classes.resize(nops);
+  for (int64_t i = 0; i < nops; i++) B->order_persistent[i] = B->order_classes[i] = (int32_t)i;
+  std::stable_sort(B->order_persistent.begin(), B->order_persistent.end(),
+                   [&](int32_t x, int32_t y) { return op_cost(ops[x]) > op_cost(ops[y]); });
+  std::stable_sort(B->order_classes.begin(), B->order_classes.end(), [&](int32_t x, int32_t y) {
+    const int kx = ops[x].op * 64 + size_class(ops[x]), ky = ops[y].op * 64 + size_class(ops[y]);
+    return kx < ky;
+  });
+  for (const bigint_op &o : B->ops)
+    if (o.op == BIGINT_OP_DIVMOD) B->ws_limbs_per_cta = std::max(B->ws_limbs_per_cta, ws_limbs(o.na, o.nb, o.na));
+  const int rc = batch_configure(B);
+  if (rc != BIGINT_OK) {
+    delete B;
+    return rc;
+  }
+  *out = B;
+  return BIGINT_OK;
+}
+
+int batch_upload(bigint_batch *B, void *ws, size_t bytes, cudaStream_t st) {
+  if (!B || (!ws && B->workspace_bytes) || bytes < B->workspace_bytes) return BIGINT_ENOMEM;
+  if (((uintptr_t)ws) % 256) return BIGINT_EINVAL;
+  char *w = static_cast<char *>(ws);
+  const size_t n = B->ops.size();
+  if (n == 0) return BIGINT_OK;
+  BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->desc_off, B->ops.data(), n * sizeof(bigint_op),
+                                  cudaMemcpyHostToDevice, st));
+  BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->order_p_off, B->order_persistent.data(), n * 4,
+                                  cudaMemcpyHostToDevice, st));
+  BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->order_c_off, B->order_classes.data(), n * 4,
+                                  cudaMemcpyHostToDevice, st));
+  return BIGINT_OK;
+}
+
+int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status,
+                 void *ws, int mode, cudaStream_t st) {
+  if (!B || !in || !out) return BIGINT_EINVAL;
+  if (B->ops.empty()) return BIGINT_OK;
+  char *w = static_cast<char *>(ws);
+  const OpDev *ops = reinterpret_cast<const OpDev *>(w + B->desc_off);
+  uint64_t *scratch = reinterpret_cast<uint64_t *>(w + B->scratch_off);
+  if (mode == BIGINT_BATCH_PERSISTENT) {
+    const Launch &P = B->persistent;
+    int *queue = reinterpret_cast<int *>(w + B->queue_off);
+    BIGINT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
+    k_batch<<<P.ctas, P.threads, (size_t)P.smem_words * 4, st>>>(
+        ops, reinterpret_cast<const int32_t *>(w + B->order_p_off), 0, P.count, in, out, status,
+        scratch, B->ws_limbs_per_cta, queue, P.smem_words);
+    return bigint_launch_status();
+  }
+  if (mode != BIGINT_BATCH_PER_CLASS) return BIGINT_EINVAL;
+  for (const Launch &L : B->classes) {
+    k_batch<<<L.ctas, L.threads, (size_t)L.smem_words * 4, st>>>(
+        ops, reinterpret_cast<const int32_t *>(w + B->order_c_off), L.first, L.count, in, out,
+        status, scratch, B->ws_limbs_per_cta, nullptr, L.smem_words);
+    const int rc = bigint_launch_status();
+    if (rc != BIGINT_OK) return rc;
+  }
+  return BIGINT_OK;
+}
+
+size_t batch_workspace_bytes(const bigint_batch *B) { return B ? B->workspace_bytes : 0; }
+
+int batch_retune(bigint_batch *B, int threads) {
+  if (!B) return BIGINT_EINVAL;
+  B->threads_override = threads;
+  return batch_configure(B);
+}
+
+void batch_destroy(bigint_batch *B) { delete B; }
+
+}  // namespace bigint

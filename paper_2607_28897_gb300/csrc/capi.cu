@@ -21,6 +21,18 @@ size_t divmod_workspace(int64_t count, int nu, int nv);
 int launch_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count, int nv,
                  int h, int nw, void *ws, size_t ws_bytes, cudaStream_t st);
 size_t shinv_workspace(int64_t count, int nv, int h);
+int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out);
+size_t batch_workspace_bytes(const bigint_batch *B);
+int batch_upload(bigint_batch *B, void *ws, size_t bytes, cudaStream_t st);
+int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status,
+                 void *ws, int mode, cudaStream_t st);
+void batch_destroy(bigint_batch *B);
+int tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na, int nb,
+             cudaStream_t st, int *best_variant);
+int tune_batch(bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status, void *ws,
+               size_t bytes, cudaStream_t st, int *best_threads);
+int tuning_save(const char *path);
+int tuning_load(const char *path);
 }  // namespace bigint
 
 using namespace bigint;
@@ -123,6 +135,43 @@ int bigint_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count,
   return launch_shinv(v, w, status, count, nv, h, nw, workspace, workspace_bytes,
                       as_stream(stream));
 }
+
+int bigint_batch_create(const bigint_op *ops_host, int64_t nops, bigint_batch **batch) {
+  return batch_create(ops_host, nops, batch);
+}
+
+size_t bigint_batch_workspace(const bigint_batch *batch) { return batch_workspace_bytes(batch); }
+
+int bigint_batch_upload(bigint_batch *batch, void *workspace, size_t bytes, void *stream) {
+  if (!batch) return BIGINT_EINVAL;
+  return batch_upload(batch, workspace, bytes, as_stream(stream));
+}
+
+int bigint_batch_launch(const bigint_batch *batch, const uint64_t *in_pool, uint64_t *out_pool,
+                        int32_t *status, void *workspace, int mode, void *stream) {
+  if (!batch) return BIGINT_EINVAL;
+  return batch_launch(batch, in_pool, out_pool, status, workspace, mode, as_stream(stream));
+}
+
+int bigint_batch_tune(bigint_batch *batch, const uint64_t *in_pool, uint64_t *out_pool,
+                      int32_t *status, void *workspace, size_t bytes, void *stream,
+                      int *best_threads) {
+  if (!batch || !in_pool || !out_pool) return BIGINT_EINVAL;
+  return tune_batch(batch, in_pool, out_pool, status, workspace, bytes, as_stream(stream),
+                    best_threads);
+}
+
+void bigint_batch_destroy(bigint_batch *batch) { batch_destroy(batch); }
+
+int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                    int32_t na, int32_t nb, void *stream, int *best_variant) {
+  if (count < 1 || count > 0x7fffffff || na < 1 || nb < 1) return BIGINT_EINVAL;
+  if (na > mul_max_limbs() || nb > mul_max_limbs() || !a || !b || !out) return BIGINT_EINVAL;
+  return tune_mul(a, b, out, count, na, nb, as_stream(stream), best_variant);
+}
+
+int bigint_tuning_save(const char *path) { return path ? tuning_save(path) : BIGINT_EINVAL; }
+int bigint_tuning_load(const char *path) { return path ? tuning_load(path) : BIGINT_EINVAL; }
 
 int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);

@@ -1,0 +1,363 @@
+// divcore.cuh -- device-side building blocks of the shifted-inverse division
+// (Sec. V-C, Fig. 6), shared by the uniform-batch kernel (divmod.cu) and the
+// ragged mixed-op batch kernel (batch.cu).  The algorithm and its reading of
+// the paper are described at the top of divmod.cu.
+#pragma once
+#include "blockops.cuh"
+#include "mulcore.cuh"
+
+namespace bigint {
+namespace divc {
+namespace {  // internal linkage: this header is included by several units
+
+constexpr int DRB = 28, DQ = 8, DF = 128;  // product variant used inside division
+constexpr int MAX_CORRECTIONS = 8;
+
+// ---------------------------------------------------------------------------
+// One-thread long division for the Newton start value (tiny operands:
+// u <= 7 limbs, v <= 5 limbs).  Knuth's Algorithm D with 64-bit digits and
+// 128-bit intermediates.  q[0 .. nu-nv] receives floor(u / v); v[nv-1] != 0.
+// ---------------------------------------------------------------------------
+__device__ void small_div(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q) {
+  typedef unsigned __int128 u128;
+  for (int j = 0; j <= nu - nv; j++) q[j] = 0;
+  if (nu < nv) return;
+  if (nv == 1) {
+    u128 rem = 0;
+    for (int i = nu - 1; i >= 0; i--) {
+      const u128 cur = (rem << 64) | u[i];
+      q[i] = (uint64_t)(cur / v[0]);
+      rem = cur % v[0];
+    }
+    return;
+  }
+  uint64_t vn[5], un[8];
+  const int s = __clzll(v[nv - 1]);
+  for (int i = nv - 1; i > 0; i--) vn[i] = (v[i] << s) | (s ? v[i - 1] >> (64 - s) : 0);
+  vn[0] = v[0] << s;
+  un[nu] = s ? u[nu - 1] >> (64 - s) : 0;
+  for (int i = nu - 1; i > 0; i--) un[i] = (u[i] << s) | (s ? u[i - 1] >> (64 - s) : 0);
+  un[0] = u[0] << s;
+  const u128 B = (u128)1 << 64;
+  for (int j = nu - nv; j >= 0; j--) {
+    const u128 num = ((u128)un[j + nv] << 64) | un[j + nv - 1];
+    u128 qh = num / vn[nv - 1];
+    u128 rh = num % vn[nv - 1];
+    while (qh >= B || qh * vn[nv - 2] > ((rh << 64) | un[j + nv - 2])) {
+      qh--;
+      rh += vn[nv - 1];
+      if (rh >= B) break;
+    }
+    u128 borrow = 0, carry = 0;
+    for (int i = 0; i < nv; i++) {
+      const u128 p = qh * vn[i] + carry;
+      carry = p >> 64;
+      const u128 t = (u128)un[i + j] - (uint64_t)p - borrow;
+      un[i + j] = (uint64_t)t;
+      borrow = (t >> 64) ? 1 : 0;
+    }
+    const u128 t = (u128)un[j + nv] - carry - borrow;
+    un[j + nv] = (uint64_t)t;
+    if (t >> 64) {  // estimate one too large: add back
+      qh--;
+      u128 c = 0;
+      for (int i = 0; i < nv; i++) {
+        const u128 s2 = (u128)un[i + j] + vn[i] + c;
+        un[i + j] = (uint64_t)s2;
+        c = s2 >> 64;
+      }
+      un[j + nv] += (uint64_t)c;
+    }
+    q[j] = (uint64_t)qh;
+  }
+}
+
+// Per-instance workspace, in limbs.
+struct Work {
+  uint64_t *w, *wn, *p, *d, *qh, *r, *tmp;
+  int cap_w, cap_p, cap_d;
+};
+
+__host__ __device__ inline int ws_cap_w(int nu, int nv, int h) {
+  const int H = nu > h ? nu : h;
+  return H + 8;
+}
+__host__ __device__ inline int ws_cap_p(int nu, int nv, int h) {
+  const int H = nu > h ? nu : h;
+  return 2 * H + nv + 16;
+}
+__host__ __device__ inline int ws_cap_d(int nu, int nv, int h) {
+  const int H = nu > h ? nu : h;
+  return H + nv + 16;
+}
+// limbs per instance (rounded to 32 limbs = 256 bytes)
+__host__ __device__ inline int64_t ws_limbs(int nu, int nv, int h) {
+  const int64_t t = 4 * (int64_t)ws_cap_w(nu, nv, h) + 2 * (int64_t)ws_cap_p(nu, nv, h) +
+                    ws_cap_d(nu, nv, h) + (nv + 8);
+  return (t + 31) / 32 * 32;
+}
+
+__device__ Work carve(uint64_t *base, int nu, int nv, int h) {
+  Work W;
+  W.cap_w = ws_cap_w(nu, nv, h);
+  W.cap_p = ws_cap_p(nu, nv, h);
+  W.cap_d = ws_cap_d(nu, nv, h);
+  uint64_t *p = base;
+  W.w = p; p += W.cap_w;
+  W.wn = p; p += W.cap_w;
+  W.qh = p; p += W.cap_w;
+  W.p = p; p += W.cap_p;
+  W.tmp = p; p += W.cap_p;
+  W.d = p; p += W.cap_d;
+  W.r = p; p += W.cap_w;
+  return W;
+}
+
+// ---------------------------------------------------------------------------
+// Product of arbitrary (limb) sizes: one blk_mul when both operands fit the
+// shared-memory budget, otherwise a sum of slice products, each added into
+// place (out must not overlap x, y or tmp).  Writes out[0..nout).
+// ---------------------------------------------------------------------------
+__device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
+                        int nout, uint64_t *tmp, uint32_t *smem, int smem_words) {
+  if (nx <= 0 || ny <= 0) {
+    blk_zero(out, nout);
+    __syncthreads();
+    return;
+  }
+  if (blk_mul_smem_words<DRB, DQ>(nx, ny) <= smem_words) {
+    blk_mul<DRB, DQ, DF>(x, nx, y, ny, out, nout, smem);
+    return;
+  }
+  // slice both operands into pieces of s limbs whose products fit
+  int s = 8192;
+  while (s > 64 && blk_mul_smem_words<DRB, DQ>(s, s) > smem_words) s -= 64;
+  uint32_t *scr = smem;  // blk_addsub scratch (the slice product is done)
+  blk_zero(out, nout);
+  __syncthreads();
+  for (int i0 = 0; i0 < nx; i0 += s) {
+    const int sx = nx - i0 < s ? nx - i0 : s;
+    for (int j0 = 0; j0 < ny; j0 += s) {
+      const int sy = ny - j0 < s ? ny - j0 : s;
+      const int off = i0 + j0;
+      if (off >= nout) continue;
+      const int len = sx + sy;
+      blk_mul<DRB, DQ, DF>(x + i0, sx, y + j0, sy, tmp, len, smem);
+      const int n = nout - off;
+      uint64_t *o = out + off;
+      auto load = [&](int j) { return make_ulonglong2(o[j], j < len ? tmp[j] : 0ull); };
+      auto store = [&](int j, uint64_t v) { o[j] = v; };
+      blk_addsub<false>(n, 0u, load, store, scr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The Newton start value: w = floor(B^(2l) / V) with V = floor(v / B^(k-l))
+// + 1 (k >= l) or V = v B^(l-k) (k < l).  Thread 0 computes, all wait.
+// ---------------------------------------------------------------------------
+__device__ void newton_start(const uint64_t *v, int k, int l, uint64_t *w, int cap_w) {
+  if (threadIdx.x == 0) {
+    uint64_t V[6] = {0, 0, 0, 0, 0, 0}, U[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Qt[8];
+    int nV;
+    if (k >= l) {
+      for (int i = 0; i <= l; i++) V[i] = v[k - l + i];
+      // V + 1 (may carry into limb l+1)
+      int i = 0;
+      while (i <= l && ++V[i] == 0) i++;
+      nV = (i > l) ? l + 2 : l + 1;
+      if (i > l) V[l + 1] = 1;
+    } else {
+      for (int i = 0; i <= k; i++) V[l - k + i] = v[i];
+      nV = l + 1;
+    }
+    U[2 * l] = 1;  // B^(2l)
+    small_div(U, 2 * l + 1, V, nV, Qt);
+    const int nq = 2 * l + 1 - nV + 1;
+    for (int i = 0; i < cap_w; i++) w[i] = i < nq ? Qt[i] : 0;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// One Newton step (Fig. 6 step) with the divisor vt (nvt limbs):
+//   e = hp - m;  d = B^e - vt w;  w' = w B^m +- round(w |d| / B^(hp - 2m)),
+// floor for d >= 0, ceiling for d < 0.  w is in W.w (prec nw), the result
+// goes to W.wn and the two buffers are swapped.  Returns prec(w').
+// ---------------------------------------------------------------------------
+__device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, int nw,
+                           uint32_t *smem, int smem_words, uint32_t *scr) {
+  const int e = hp - m;
+  // P1 = vt * w
+  const int n1 = nvt + nw;
+  mul_any(vt, nvt, W.w, nw, W.p, n1, W.tmp, smem, smem_words);
+  const int pp = blk_prec(W.p, n1, scr);
+  const bool neg = pp > e;  // vt w >= B^e (d <= 0; d = 0 gives y = 0 either way)
+  // D = |B^e - P1|
+  int nd;
+  {
+    uint64_t *P = W.p, *D = W.d;
+    if (!neg) {  // B^e - P1 over e limbs (P1 < B^e, P1 > 0)
+      auto load = [&](int j) { return make_ulonglong2(0ull, j < n1 ? P[j] : 0ull); };
+      auto store = [&](int j, uint64_t x) { D[j] = x; };
+      blk_addsub<true>(e, 0u, load, store, scr);
+      nd = e;
+    } else {  // P1 - B^e over pp limbs
+      auto load = [&](int j) { return make_ulonglong2(P[j], j == e ? 1ull : 0ull); };
+      auto store = [&](int j, uint64_t x) { D[j] = x; };
+      blk_addsub<true>(pp, 0u, load, store, scr);
+      nd = pp;
+    }
+  }
+  nd = blk_prec(W.d, nd, scr);
+  // P2 = w * D ; y = P2 >> s limbs, s = hp - 2m
+  const int s = hp - 2 * m;
+  const int n2 = nw + nd;
+  uint32_t cin = 0;
+  if (nd > 0) {
+    mul_any(W.w, nw, W.d, nd, W.p, n2, W.tmp, smem, smem_words);
+    if (neg) cin = (uint32_t)blk_any_nonzero(W.p, s < n2 ? s : n2, scr);  // ceiling
+  }
+  const uint64_t *Y = W.p + s;
+  const int ny = nd > 0 ? (n2 - s > 0 ? n2 - s : 0) : 0;
+  // w' = w B^m +- (y + cin)
+  const int nout = (nw + m > ny ? nw + m : ny) + 1;
+  {
+    const uint64_t *w = W.w;
+    uint64_t *wn = W.wn;
+    auto load = [&](int j) {
+      const uint64_t x = (j >= m && j - m < nw) ? w[j - m] : 0ull;
+      return make_ulonglong2(x, j < ny ? Y[j] : 0ull);
+    };
+    auto store = [&](int j, uint64_t x) { wn[j] = x; };
+    if (neg) blk_addsub<true>(nout, cin, load, store, scr);
+    else blk_addsub<false>(nout, 0u, load, store, scr);
+  }
+  uint64_t *t = W.w;
+  W.w = W.wn;
+  W.wn = t;
+  return blk_prec(W.w, nout, scr);
+}
+
+// w ~ B^h / v (0 <= B^h/v - w < 2 before the final correction); returns
+// prec(w).  v has precision k+1.
+__device__ int shinv_newton(const uint64_t *v, int k, int h, Work &W, uint32_t *smem,
+                            int smem_words, uint32_t *scr) {
+  const int L = h - k;
+  int l = L < 3 ? L : 3;
+  newton_start(v, k, l, W.w, W.cap_w);
+  int nw = blk_prec(W.w, l + 2, scr);
+  while (l < L) {
+    const int m = (l - 2 < L - l) ? l - 2 : L - l;
+    const int t = (k < l + m + 2) ? k : l + m + 2;
+    nw = newton_step(t + l + m, m, v + (k - t), t + 1, W, nw, smem, smem_words, scr);
+    l += m;
+  }
+  return nw;
+}
+
+// R = R mod B^(kv+1) holds x - Q v for some Q in W.qh (prec nq <= cap);
+// bring it into [0, v).  Returns 0 or BIGINT_EINTERNAL.
+__device__ int correct(const uint64_t *v, int kv, uint64_t *R, uint64_t *Qh, int nqcap,
+                       uint32_t *scr) {
+  const int nr = kv + 1;
+  for (int it = 0; it < 2 * MAX_CORRECTIONS; it++) {
+    __syncthreads();
+    const bool negative = (R[kv] >> 63) != 0;
+    int dir = 0;  // +1: r -= v, q++ ; -1: r += v, q--
+    if (negative) {
+      dir = -1;
+    } else {
+      // R >= v ?  (v has kv limbs, R has kv+1)
+      int top = 0;
+      for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        const uint64_t vj = j < kv ? v[j] : 0ull;
+        if (R[j] != vj) top = j + 1;
+      }
+      top = blk_max(top, scr);
+      if (top == 0) dir = 1;  // R == v
+      else {
+        const uint64_t vj = top - 1 < kv ? v[top - 1] : 0ull;
+        dir = R[top - 1] > vj ? 1 : 0;
+      }
+    }
+    if (dir == 0) return BIGINT_OK;
+    {
+      auto load = [&](int j) { return make_ulonglong2(R[j], j < kv ? v[j] : 0ull); };
+      auto store = [&](int j, uint64_t x) { R[j] = x; };
+      if (dir > 0) blk_addsub<true>(nr, 0u, load, store, scr);
+      else blk_addsub<false>(nr, 0u, load, store, scr);
+    }
+    {
+      auto load = [&](int j) { return make_ulonglong2(Qh[j], j == 0 ? 1ull : 0ull); };
+      auto store = [&](int j, uint64_t x) { Qh[j] = x; };
+      if (dir > 0) blk_addsub<false>(nqcap, 0u, load, store, scr);
+      else blk_addsub<true>(nqcap, 0u, load, store, scr);
+    }
+  }
+  return BIGINT_EINTERNAL;
+}
+
+
+// One division q = floor(u / v), r = u - q v by the whole CTA (Sec. V-C):
+// the shifted inverse by Newton steps, q^ = floor(u w / B^h), r^ computed
+// modulo B^(k+2), exact correction.  ws: this instance's workspace region of
+// ws_limbs(nu, nv, nu) limbs.  Returns the status (0, EDIVZERO, ERANGE,
+// EINTERNAL).
+__device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q,
+                          int nq, uint64_t *r, uint64_t *ws, uint32_t *smem, int smem_words,
+                          uint32_t *scr) {
+  Work W = carve(ws, nu, nv, nu);
+  int st = BIGINT_OK;
+  const int kv = blk_prec(v, nv, scr);
+  if (kv == 0) {  // division by zero: q = r = 0
+    blk_zero(q, nq);
+    blk_zero(r, nv);
+    __syncthreads();
+    return BIGINT_EDIVZERO;
+  }
+  const int k = kv - 1;
+  const int ku = blk_prec(u, nu, scr);
+  if (ku < kv) {  // u < B^(ku) <= B^(kv-1) <= v: q = 0, r = u
+    blk_zero(q, nq);
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = j < ku ? u[j] : 0;
+    __syncthreads();
+    return BIGINT_OK;
+  }
+  const int h = ku;
+  int nw = shinv_newton(v, k, h, W, smem, smem_words, scr);
+  // q^ = floor(u w / B^h)
+  const int nz = ku + nw;
+  mul_any(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words);
+  const int nqh = nz - h > 0 ? nz - h : 0;
+  const int qcap = nqh + 1 < W.cap_w ? nqh + 1 : W.cap_w;
+  for (int j = threadIdx.x; j < qcap; j += blockDim.x) W.qh[j] = j < nqh ? W.p[h + j] : 0;
+  __syncthreads();
+  const int pq = blk_prec(W.qh, qcap, scr);
+  // r^ = (u - q^ v) mod B^(kv+1): the low kv+1 limbs of q^ v only
+  if (pq > 0) {
+    mul_any(W.qh, pq, v, kv, W.p, kv + 1, W.tmp, smem, smem_words);
+  } else {
+    blk_zero(W.p, kv + 1);
+    __syncthreads();
+  }
+  {
+    uint64_t *P = W.p, *R = W.r;
+    auto load = [&](int j) { return make_ulonglong2(j < ku ? u[j] : 0ull, P[j]); };
+    auto store = [&](int j, uint64_t x) { R[j] = x; };
+    blk_addsub<true>(kv + 1, 0u, load, store, scr);
+  }
+  st = correct(v, kv, W.r, W.qh, qcap, scr);
+  __syncthreads();
+  const int pqf = blk_prec(W.qh, qcap, scr);
+  if (pqf > nq && st == BIGINT_OK) st = BIGINT_ERANGE;
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) q[j] = j < qcap ? W.qh[j] : 0;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = j < kv ? W.r[j] : 0;
+  __syncthreads();
+  return st;
+}
+
+}  // namespace
+}  // namespace divc
+
+}  // namespace bigint

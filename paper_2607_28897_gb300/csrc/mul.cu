@@ -9,13 +9,13 @@
 
 namespace bigint {
 
-template <int RB, int Q, int F, bool ASM>
-__global__ void __launch_bounds__(Q >= 16 ? 512 : 1024)
+template <int RB, int Q, int F, bool ASM, bool PP>
+__global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
     k_mul(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
           uint64_t *__restrict__ Out, int na, int nb, int nout) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int64_t inst = blockIdx.x;
-  blk_mul<RB, Q, F, ASM>(A + inst * (int64_t)na, na, Bm + inst * (int64_t)nb, nb,
+  blk_mul<RB, Q, F, ASM, PP>(A + inst * (int64_t)na, na, Bm + inst * (int64_t)nb, nb,
                     Out + inst * (int64_t)nout, nout, smem);
 }
 
@@ -43,7 +43,7 @@ static int smem_optin() {
   return g_smem_optin;
 }
 
-template <int RB, int Q, int F, bool ASM = false>
+template <int RB, int Q, int F, bool ASM = false, bool PP = false>
 static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
                           int na, int nb, int nout, cudaStream_t st) {
   const size_t smem = sizeof(uint32_t) * (size_t)blk_mul_smem_words<RB, Q>(na, nb);
@@ -52,21 +52,32 @@ static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, i
   if (smem > (size_t)optin) return BIGINT_EINVAL;
   static bool configured = false;
   if (!configured) {
-    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F, ASM>,
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F, ASM, PP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     configured = true;
   }
-  const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 512 : 1024);
-  k_mul<RB, Q, F, ASM><<<(unsigned)count, T, smem, st>>>(a, b, out, na, nb, nout);
+  const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 640 : 1024);
+  k_mul<RB, Q, F, ASM, PP><<<(unsigned)count, T, smem, st>>>(a, b, out, na, nb, nout);
   return bigint_launch_status();
 }
 
 // Variant table (see bigint_set_variant).  Variant 0 picks by size from
 // measurements on GB300 (full-product sweep, 2^32-bit operand arrays):
-// 28-bit digits / 8-column chunks are fastest below ~2^16 bits, 29-bit
-// digits / 16-column chunks above.
+// ping-pong windows with 28-bit digits / 8-column chunks are fastest below
+// ~2^16 bits, with 29-bit digits / 16-column chunks above.
 static int g_mul_variant = 0;
-constexpr int MUL_VARIANTS = 7;
+constexpr int MUL_VARIANTS = 10;
+// Tuned variant per size class (class c: operands of [2^c, 2^(c+1)) limbs),
+// 0 = not tuned (built-in choice).  Written by bigint_tune_mul and
+// bigint_tuning_load.
+int g_mul_tuned[32] = {};
+
+int mul_size_class(int na, int nb) {
+  const int n = na > nb ? na : nb;
+  int c = 0;
+  while ((2 << c) <= n) c++;
+  return c;
+}
 
 int mul_set_variant(int v) {
   if (v < 0 || v >= MUL_VARIANTS) return BIGINT_EINVAL;
@@ -80,13 +91,17 @@ int mul_max_limbs() { return BIGINT_MUL_MAX_LIMBS; }
 int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                int nb, int nout, cudaStream_t st) {
   int v = g_mul_variant;
-  if (v == 0) v = (na > nb ? na : nb) < 1536 ? 1 : 4;
+  if (v == 0) v = g_mul_tuned[mul_size_class(na, nb)];
+  if (v == 0) v = (na > nb ? na : nb) < 1536 ? 9 : 8;
   switch (v) {
     case 2: return launch_variant<29, 8, 32>(a, b, out, count, na, nb, nout, st);
     case 3: return launch_variant<29, 4, 32>(a, b, out, count, na, nb, nout, st);
     case 4: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);
     case 5: return launch_variant<30, 8, 8>(a, b, out, count, na, nb, nout, st);
     case 6: return launch_variant<29, 8, 32, true>(a, b, out, count, na, nb, nout, st);
+    case 7: return launch_variant<28, 16, 128, false, true>(a, b, out, count, na, nb, nout, st);
+    case 8: return launch_variant<29, 16, 32, false, true>(a, b, out, count, na, nb, nout, st);
+    case 9: return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout, st);
     default: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
   }
 }

@@ -132,6 +132,82 @@ __device__ __forceinline__ void row_steps(uint64_t (&acc)[Q], const uint32_t (&W
   }
 }
 
+// Row steps with the window split in two register buffers (lo = digits
+// [base-Q, base), hi = [base, base+Q)); the caller swaps the roles of the two
+// buffers from one group to the next, so the window slides with no register
+// moves at all.
+template <int Q, int T0>
+__device__ __forceinline__ void row_steps_pp(uint64_t (&acc)[Q], const uint32_t (&lo)[Q],
+                                             const uint32_t (&hi)[Q], const uint32_t *a) {
+  if constexpr (T0 < Q) {
+    const uint4 av = *reinterpret_cast<const uint4 *>(a + T0);
+    const uint32_t a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+#pragma unroll
+      for (int q = 0; q < Q; q++) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int x = Q - (T0 + t) + q;  // window index in [1, 2Q)
+        const uint32_t w = x < Q ? lo[x] : hi[x - Q];
+        acc[q] += (uint64_t)a4[t] * (uint64_t)w;  // one IMAD.WIDE.U32
+      }
+    }
+    row_steps_pp<Q, T0 + 4>(acc, lo, hi, a);
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void load_q(uint32_t (&r)[Q], const uint32_t *p) {
+#pragma unroll
+  for (int q = 0; q < Q; q += 4) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p + q);
+    r[q] = v.x; r[q + 1] = v.y; r[q + 2] = v.z; r[q + 3] = v.w;
+  }
+}
+
+// conv_unit with ping-pong window buffers (see row_steps_pp).
+template <int RB, int Q, int F>
+__device__ __forceinline__ void conv_unit_pp(int u, int KR, int KW, const uint32_t *sRow,
+                                             const uint32_t *sW, uint64_t *out, int nout,
+                                             uint64_t *sH) {
+  static_assert(F % Q == 0, "flush interval must be a whole number of groups");
+  static_assert(F < (1 << (64 - 2 * RB)), "flush interval too long for this digit size");
+  constexpr int FG = F / Q;
+  const int NWp = KW * Q;
+  const bool pair = u < KR;
+  const int switch_g = pair ? u + 1 : -1;
+  uint64_t acc[Q], X = 0;
+  uint32_t A[Q], Bf[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) acc[q] = 0;
+  load_q<Q>(A, sW + u * Q);  // hi half of group 0
+  bool fwd = true;
+  // one group: hi/lo are the buffer roles for this group's parity
+  auto group = [&](int g, uint32_t (&hi)[Q], uint32_t (&lo)[Q]) {
+    if (g == switch_g) {  // low chunk done: continue with its partner
+      finish_chunk<RB, Q>(acc, X, u, out, nout, sH);
+#pragma unroll
+      for (int q = 0; q < Q; q++) { acc[q] = 0; hi[q] = 0; }  // window[NWp..) is padding
+      X = 0;
+      fwd = false;
+    }
+    const int base = fwd ? (u - g) * Q : NWp + (u + 1 - g) * Q;
+    const int i0 = fwd ? g * Q : (g - 1) * Q;
+    load_q<Q>(lo, sW + base - Q);
+    row_steps_pp<Q, 0>(acc, lo, hi, sRow + i0);
+    if ((g + 1) % FG == 0) normalise<RB, Q>(acc, X);
+  };
+  int g = 0;
+#pragma unroll 1
+  for (; g + 1 <= KR; g += 2) {
+    group(g, A, Bf);      // hi = A, lo = B
+    group(g + 1, Bf, A);  // hi = B (the previous lo), lo = A
+  }
+  if (g <= KR) group(g, A, Bf);
+  finish_chunk<RB, Q>(acc, X, pair ? KW + u : u, out, nout, sH);
+}
+
 template <int RB, int Q, int F, bool ASM>
 __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t *sRow,
                                           const uint32_t *sW, uint64_t *out, int nout,
@@ -182,7 +258,7 @@ __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t 
 // overlap x or y).  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
 // aligned.  Returns the carry out of limb nout-1 of the final addition
 // (0 whenever nout >= nx + ny).
-template <int RB, int Q, int F, bool ASM = false>
+template <int RB, int Q, int F, bool ASM = false, bool PP = false>
 __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
                             int nout, uint32_t *smem) {
   const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
@@ -206,7 +282,10 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
   __syncthreads();
 
   // ---- A3: convolution, one unit at a time per thread
-  for (int u = t; u < KW; u += T) conv_unit<RB, Q, F, ASM>(u, KR, KW, sRow, sW, out, nout, sH);
+  for (int u = t; u < KW; u += T) {
+    if constexpr (PP) conv_unit_pp<RB, Q, F>(u, KR, KW, sRow, sW, out, nout, sH);
+    else conv_unit<RB, Q, F, ASM>(u, KR, KW, sRow, sW, out, nout, sH);
+  }
   __syncthreads();
 
   // ---- A4: out += overflow words, one carry-scan addition

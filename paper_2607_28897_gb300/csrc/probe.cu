@@ -79,36 +79,48 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 #pragma unroll
     for (int q = 0; q < 8; q++) y[q] += acc[q];
   } else if constexpr (VARIANT == 5 || VARIANT == 6) {
-    // as 3 with the window digit as the first multiplicand and the row
-    // digit second; 5: 8 accumulators, 6: 16 accumulators
-    constexpr int QQ = VARIANT == 5 ? 8 : 16;
-    uint64_t acc[QQ];
-    uint32_t W[2 * QQ];
+    // as 3 with the row digit made warp-uniform: 5 broadcasts it from lane
+    // 0 with a shuffle, 6 reads it from a warp-uniform shared address
+    __shared__ __align__(16) uint32_t srow[64];
+    if (threadIdx.x < 64) srow[threadIdx.x] = seed * threadIdx.x + 7;
+    __syncthreads();
+    uint64_t acc[8];
+    uint32_t W[16];
 #pragma unroll
-    for (int q = 0; q < QQ; q++) acc[q] = x[q & 7];
+    for (int q = 0; q < 8; q++) acc[q] = x[q];
 #pragma unroll
-    for (int q = 0; q < 2 * QQ; q++) W[q] = x[(q + 3) & 7] + q;
+    for (int q = 0; q < 16; q++) W[q] = x[(q + 3) & 7] + q;
 #pragma unroll 1
     for (int it = 0; it < PROBE_ITERS / 8; it++) {
+      uint32_t av[8];
+      if constexpr (VARIANT == 5) {
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        const uint32_t a = x[t] ^ (uint32_t)it;
-#pragma unroll
-        for (int q = 0; q < QQ; q++)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(W[QQ - t + q]), "r"(a));
+        for (int t = 0; t < 8; t++) av[t] = __shfl_sync(FULL, x[t] ^ (uint32_t)it, 0);
+      } else {
+        const uint4 a0 = *reinterpret_cast<const uint4 *>(srow + ((it * 8) & 56));
+        const uint4 a1 = *reinterpret_cast<const uint4 *>(srow + ((it * 8) & 56) + 4);
+        av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+        av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
       }
 #pragma unroll
-      for (int q = 0; q < QQ; q++) W[QQ + q] = W[q] + (uint32_t)it;
+      for (int t = 0; t < 8; t++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(av[t]), "r"(W[8 - t + q]));
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++) W[8 + q] = W[q] + (uint32_t)it;
     }
 #pragma unroll
-    for (int q = 0; q < QQ; q++) y[q & 7] += acc[q];
+    for (int q = 0; q < 8; q++) y[q] += acc[q];
   } else {
-    // as 0 with the operands swapped (constant first, varying second)
+    // as 0 with a per-thread (not warp-uniform) multiplier
+    const uint32_t mt = m ^ threadIdx.x;
 #pragma unroll 1
     for (int it = 0; it < PROBE_ITERS; it++) {
 #pragma unroll
       for (int k = 0; k < 8; k++)
-        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(m), "r"(x[k]));
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(x[k]), "r"(mt));
     }
   }
   __syncthreads();
@@ -121,8 +133,7 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 
 // Operations per thread for one probe launch.
 static double probe_ops_per_thread(int variant) {
-  if (variant == 3 || variant == 4 || variant == 5) return (double)(PROBE_ITERS / 8) * 64;
-  if (variant == 6) return (double)(PROBE_ITERS / 8) * 128;
+  if (variant >= 3 && variant <= 6) return (double)(PROBE_ITERS / 8) * 64;
   return (double)PROBE_ITERS * 8;
 }
 

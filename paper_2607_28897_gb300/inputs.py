@@ -200,3 +200,67 @@ def config_sweep_torch(n: int, seed: int = 2, batch: int | None = None, device="
     a = limbs_torch(seed * 100 + n, batch, n, True, device)
     b = limbs_torch(seed * 100 + n + 50, batch, n, True, device)
     return a, b
+
+
+# ---------------------------------------------------------------------------
+# Ragged mixed-op batches (the batched form): descriptors + pool layout.
+# ---------------------------------------------------------------------------
+OP_ADD, OP_SUB, OP_MUL, OP_DIVMOD = 1, 2, 3, 4
+
+
+def ragged_ops(seed: int, count: int, min_limbs: int = 512, max_limbs: int = 8192,
+               mix=(0.40, 0.15, 0.15, 0.30)):
+    """Operation descriptors of a ragged batch: sizes 2^U bits, U ~
+    Uniform[15, 19] rounded to limbs (clamped to [min_limbs, max_limbs]),
+    ops drawn with probabilities mix = (mul, add, sub, divmod); a divmod
+    draws n_v from the size law and n_u uniform in [n_v, 2 n_v].  Operands
+    are laid out back to back in an input pool, results in an output pool.
+    Returns (ops, in_limbs, out_limbs) with ops a numpy array of the
+    bigint_op layout."""
+    import numpy as np
+
+    dt = np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("reserved", "<i4"),
+                   ("a", "<i8"), ("b", "<i8"), ("o1", "<i8"), ("o2", "<i8")])
+    n = ragged_sizes(seed, count, min_limbs=min_limbs, max_limbs=max_limbs)
+    if min_limbs < 512 or max_limbs < 8192:  # small test batches: spread over the range
+        u = (uniform(seed + 3, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+        n = np.clip(np.rint(min_limbs * (max_limbs / min_limbs) ** u), min_limbs, max_limbs)
+        n = n.astype(np.int64)
+    u01 = (uniform(seed + 1, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    c = np.cumsum(mix)
+    op = np.where(u01 < c[0], OP_MUL, np.where(u01 < c[1], OP_ADD,
+                  np.where(u01 < c[2], OP_SUB, OP_DIVMOD))).astype(np.int32)
+    u2 = (uniform(seed + 2, count) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    na = n.copy()
+    nb = n.copy()
+    div = op == OP_DIVMOD
+    na[div] = n[div] + np.floor(u2[div] * (n[div] + 1)).astype(np.int64)  # n_u in [n_v, 2 n_v]
+    ops = np.zeros(count, dtype=dt)
+    ops["op"], ops["na"], ops["nb"] = op, na, nb
+    in_sizes = na + nb
+    a_off = np.concatenate([[0], np.cumsum(in_sizes)[:-1]])
+    ops["a"], ops["b"] = a_off, a_off + na
+    nq = np.maximum(na - nb + 1, 1)
+    out_sizes = np.where(op == OP_MUL, na + nb, np.where(div, nq + nb, na))
+    o_off = np.concatenate([[0], np.cumsum(out_sizes)[:-1]])
+    ops["o1"] = o_off
+    ops["o2"] = np.where(div, o_off + nq, 0)
+    return ops, int(in_sizes.sum()), int(out_sizes.sum())
+
+
+def ragged_pool(seed: int, ops, in_limbs: int, device=None):
+    """Input pool of uniform limbs with every operand's top limb nonzero
+    (numpy when device is None, else a torch int64 tensor on device)."""
+    import numpy as np
+
+    tops = np.concatenate([ops["a"] + ops["na"] - 1, ops["b"] + ops["nb"] - 1])
+    if device is None:
+        pool = uniform(seed, in_limbs)
+        pool[tops] |= np.uint64(1)
+        return pool
+    import torch
+
+    pool = uniform_torch(seed, in_limbs, device)
+    t = torch.from_numpy(tops.astype(np.int64)).to(device)
+    pool[t] = pool[t] | 1
+    return pool

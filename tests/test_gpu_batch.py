@@ -1,0 +1,125 @@
+"""Ragged mixed-op batches: persistent (work queue) and per-class launches
+give bit-exactly the oracle's results, and every result is the same alone
+and in the mix."""
+import numpy as np
+import pytest
+
+from helpers import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_results(orc, ops, pool):
+    """Expected output pool and statuses from the oracle, op by op."""
+    out = {}
+    st = np.zeros(len(ops), dtype=np.int32)
+    for i, o in enumerate(ops):
+        a = pool[o["a"]:o["a"] + o["na"]]
+        b = pool[o["b"]:o["b"] + o["nb"]]
+        if o["op"] == 1:
+            r, c = orc.add(a, b)
+            out[i] = (r,)
+            st[i] = c
+        elif o["op"] == 2:
+            r, c = orc.sub(a, b)
+            out[i] = (r,)
+            st[i] = c
+        elif o["op"] == 3:
+            out[i] = (orc.mul(a, b),)
+        else:
+            q, r, s = orc.divmod_(a, b)
+            out[i] = (q, r)
+            st[i] = {0: 0, 2: -2, 1: -7}[s]
+    return out, st
+
+
+def check(ops, got_pool, got_st, exp, exp_st):
+    assert np.array_equal(got_st, exp_st)
+    for i, o in enumerate(ops):
+        if o["op"] == 4:
+            q, r = exp[i]
+            assert np.array_equal(got_pool[o["o1"]:o["o1"] + q.size], q), i
+            assert np.array_equal(got_pool[o["o2"]:o["o2"] + r.size], r), i
+        else:
+            (r,) = exp[i]
+            assert np.array_equal(got_pool[o["o1"]:o["o1"] + r.size], r), i
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_small_ragged(orc, mode):
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    ops, nin, nout = inputs.ragged_ops(7, 300, min_limbs=1, max_limbs=700)
+    pool = inputs.ragged_pool(8, ops, nin)
+    exp, exp_st = oracle_results(orc, ops, pool)
+    dpool = to_dev(pool)[None, :].view(-1)
+    dout = torch.zeros(nout, dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+    B = bi.Batch(ops)
+    B.launch(dpool, dout, st, mode=mode)
+    torch.cuda.synchronize()
+    check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
+
+
+def test_batch_alone_equals_mix(orc):
+    """Each operation run alone (a batch of one) gives the same bits as in
+    the mixed batch (persistent form)."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    ops, nin, nout = inputs.ragged_ops(11, 60, min_limbs=8, max_limbs=2000)
+    pool = to_dev(inputs.ragged_pool(12, ops, nin)).view(-1)
+    mix_out = torch.zeros(nout, dtype=torch.int64, device="cuda")
+    mix_st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+    bi.Batch(ops).launch(pool, mix_out, mix_st)
+    for i in range(len(ops)):
+        one = ops[i:i + 1].copy()
+        alone_out = torch.zeros(nout, dtype=torch.int64, device="cuda")
+        alone_st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        bi.Batch(one).launch(pool, alone_out, alone_st)
+        o = ops[i]
+        n_out = {1: o["na"], 2: o["na"], 3: o["na"] + o["nb"]}.get(int(o["op"]), 0)
+        if o["op"] == 4:
+            nq = max(o["na"] - o["nb"] + 1, 1)
+            n_out = nq + o["nb"]
+        s = slice(int(o["o1"]), int(o["o1"]) + int(n_out))
+        assert torch.equal(alone_out[s], mix_out[s]), i
+        assert int(alone_st[0]) == int(mix_st[i]), i
+
+
+def test_batch_tune_and_graph(orc):
+    """The autotuner picks a CTA size; a CUDA-graph replay of the persistent
+    launch gives the oracle's results."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    ops, nin, nout = inputs.ragged_ops(21, 120, min_limbs=16, max_limbs=1500)
+    pool = inputs.ragged_pool(22, ops, nin)
+    exp, exp_st = oracle_results(orc, ops, pool)
+    dpool = to_dev(pool).view(-1)
+    dout = torch.zeros(nout, dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+    B = bi.Batch(ops)
+    best = B.tune(dpool, dout, st)
+    assert best in (256, 384, 512, 640)
+    dout.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        B.launch(dpool, dout, st, stream=s)  # warm-up on the capture stream
+        torch.cuda.synchronize()
+        dout.zero_()
+        with torch.cuda.graph(g, stream=s):
+            B.launch(dpool, dout, st, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
+    bi.set_variant(0, 0)
