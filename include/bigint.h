@@ -115,6 +115,28 @@ int bigint_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q,
 /* Bytes of device workspace bigint_divmod needs for this batch shape. */
 size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv);
 
+/* Division for callers that cannot allocate device memory (no counterpart
+ * in the paper: it exists for callers that may not call cudaMalloc, such as
+ * a host application that gives this library a fixed memory budget, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation).  Same arguments, results and per-instance status as
+ * bigint_divmod, without the workspace: the scratch is one file-scope
+ * __device__ array of bigint_divmod_noalloc_scratch_bytes() bytes (32 MiB)
+ * that every GPU loading the library holds until the process exits.  It
+ * allocates nothing itself.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ * - Batches larger than the array holds run as consecutive launches on
+ *   `stream`; a shape whose single instance needs more scratch than the
+ *   array is rejected with BIGINT_ENOMEM.
+ * - All calls share the array and nothing in it needs to start at zero;
+ *   calls that overlap on the GPU (different streams, or several host
+ *   threads) race on it and must be serialised by the caller.            */
+int bigint_divmod_noalloc(const uint64_t *u, const uint64_t *v, uint64_t *q,
+                          uint64_t *r, int32_t *status, int64_t count,
+                          int32_t nu, int32_t nv, void *stream);
+size_t bigint_divmod_noalloc_scratch_bytes(void);
+
 /* Shifted inverse w = floor(B^h / v) (Sec. V-C; the Newton loop of Fig. 6).
  * v: count*nv limbs, w: count*nw limbs.  status as for bigint_divmod
  * (BIGINT_ERANGE if the inverse needs more than nw limbs).

@@ -15,7 +15,7 @@ import ctypes
 import os
 
 __all__ = [
-    "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "shinv",
+    "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "divmod_noalloc", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
     "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
     "MAX_LIMBS", "MUL_MAX_LIMBS",
@@ -41,6 +41,8 @@ SIGNATURES = {
     "bigint_mul_lo": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P], ctypes.c_int),
     "bigint_divmod": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_divmod_workspace": ([_I64, _I32, _I32], _SZ),
+    "bigint_divmod_noalloc": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "bigint_divmod_noalloc_scratch_bytes": ([], _SZ),
     "bigint_shinv": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_shinv_workspace": ([_I64, _I32, _I32], _SZ),
     "bigint_batch_create": ([_P, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -214,6 +216,24 @@ def divmod(u, v, q=None, r=None, status=None, workspace=None, stream=None):
                               workspace.numel() * workspace.element_size(),
                               _stream_ptr(stream))
     _check(rc, "bigint_divmod")
+    return q, r, status
+
+
+def divmod_noalloc(u, v, q=None, r=None, status=None, stream=None):
+    """As divmod, with the library's own fixed scratch instead of a caller
+    workspace (for callers that cannot allocate; see bigint.h)."""
+    torch = _torch()
+    u, v = _dev_tensor(u, "u"), _dev_tensor(v, "v")
+    count, nu = u.shape
+    nv = v.shape[1]
+    nq = max(nu - nv + 1, 1)
+    q = _empty_like_limbs(u, count, nq) if q is None else _dev_tensor(q, "q")
+    r = _empty_like_limbs(u, count, nv) if r is None else _dev_tensor(r, "r")
+    if status is None:
+        status = torch.empty(count, dtype=torch.int32, device=u.device)
+    rc = load().bigint_divmod_noalloc(u.data_ptr(), v.data_ptr(), q.data_ptr(), r.data_ptr(),
+                                      status.data_ptr(), count, nu, nv, _stream_ptr(stream))
+    _check(rc, "bigint_divmod_noalloc")
     return q, r, status
 
 
