@@ -48,6 +48,13 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sizes", default=",".join(str(n) for n in SWEEP))
+    p.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving"],
+                   help="sweep: the headline step (default); batched: the ragged mixed-op "
+                        "batch in one persistent launch vs one launch per size class; "
+                        "serving: continuous batching vs per-request launches")
+    p.add_argument("--batch-ops", type=int, default=200000)
+    p.add_argument("--requests", type=int, default=20000)
+    p.add_argument("--rates", default="5000,20000,50000,100000,200000")
     return p.parse_args()
 
 
@@ -257,6 +264,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
 
     import torch
@@ -518,6 +531,90 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
         dt = float(t.item())
     return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def run_batched(args):
+    """The batched form: ragged instances (sizes log-uniform over 2^15..2^19
+    bits; 40 % mul, 15 % add, 15 % sub, 30 % divmod) in one persistent launch
+    with a device-side work queue (tuned CTA size, CUDA-graph replay) against
+    one launch per (op, size class)."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    bi.load()
+    count = args.batch_ops
+    ops, nin, nout = inputs.ragged_ops(4, count)
+    pool = inputs.ragged_pool(5, ops, nin, device="cuda")
+    out = torch.zeros(nout, dtype=torch.int64, device="cuda")
+    st = torch.zeros(count, dtype=torch.int32, device="cuda")
+    B = bi.Batch(ops)
+
+    def best_of(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return min(times)
+
+    reps = max(args.steps, 1)
+    t_class = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PER_CLASS), reps)
+    ref = out.clone()
+    t_pers = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PERSISTENT), reps)
+    threads = B.tune(pool, out, st)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        B.launch(pool, out, st, stream=s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            B.launch(pool, out, st, stream=s)
+    t_graph = best_of(lambda: g.replay(), reps)
+    same = bool(torch.equal(out, ref))
+    units = ops["na"].astype(float) * ops["nb"]
+    line = {"metric": "batched form: ragged mixed-op instances per second", "value": count / (t_graph * 1e-3),
+            "unit": "ops/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{count} ragged instances, 2^15..2^19 bits log-uniform, "
+                                   "40% mul / 15% add / 15% sub / 30% divmod (n_u in [n_v, 2 n_v])"},
+            "per_class_ms": t_class, "persistent_ms": t_pers, "persistent_tuned_graph_ms": t_graph,
+            "tuned_threads": threads, "speedup_vs_per_class": t_class / t_graph,
+            "results_identical_across_forms": same}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Continuous batching against per-request launches at Poisson arrival
+    rates; throughput and p50/p99 latency."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import serve
+
+    bi.load()
+    res = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        w = serve.make_workload(41, args.requests, rate)
+        serve.run_continuous(serve.make_workload(42, 200, rate))  # warm-up
+        c = serve.run_continuous(w)
+        p = serve.run_per_request(w, limit=min(args.requests, 5000))
+        res.append({"rate": rate, "continuous": {k: c[k] for k in ("throughput", "p50_ms", "p99_ms")},
+                    "per_request": {k: p[k] for k in ("throughput", "p50_ms", "p99_ms")},
+                    "per_request_sample": p["requests"]})
+        torch.cuda.empty_cache()
+    line = {"metric": "serving: requests/s and p50/p99 latency", "value": max(r["continuous"]["throughput"] for r in res),
+            "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"{args.requests} requests per rate, 50% mul / 50% divmod, "
+                                   "sizes 2^15..2^19 bits log-uniform, HBM budget 64 GiB"},
+            "rates": res}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -227,6 +227,9 @@ int bigint_tuning_load(const char *path);
  *   variant 6: as 2, each digit product written as explicit mad.wide.u32
  *   variants 7, 8, 9: as 1 with 16-column chunks, as 4, as 1 -- with the
  *   sliding window held in two alternating register buffers (no moves)
+ *   variants 10, 11: one level of Karatsuba (square full products of at
+ *   least 64 limbs; otherwise variant 8) over half products of variant 8,
+ *   resp. variant 9
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 

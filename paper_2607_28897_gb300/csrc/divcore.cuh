@@ -10,7 +10,7 @@ namespace bigint {
 namespace divc {
 namespace {  // internal linkage: this header is included by several units
 
-constexpr int DRB = 28, DQ = 8, DF = 128;  // product variant used inside division
+constexpr int DRB = 29, DQ = 16, DF = 32;  // product variant used inside division
 constexpr int MAX_CORRECTIONS = 8;
 
 // ---------------------------------------------------------------------------
@@ -126,7 +126,7 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
     return;
   }
   if (blk_mul_smem_words<DRB, DQ>(nx, ny) <= smem_words) {
-    blk_mul<DRB, DQ, DF>(x, nx, y, ny, out, nout, smem);
+    blk_mul<DRB, DQ, DF, false, true>(x, nx, y, ny, out, nout, smem);
     return;
   }
   // slice both operands into pieces of s limbs whose products fit
@@ -142,7 +142,7 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
       const int off = i0 + j0;
       if (off >= nout) continue;
       const int len = sx + sy;
-      blk_mul<DRB, DQ, DF>(x + i0, sx, y + j0, sy, tmp, len, smem);
+      blk_mul<DRB, DQ, DF, false, true>(x + i0, sx, y + j0, sy, tmp, len, smem);
       const int n = nout - off;
       uint64_t *o = out + off;
       auto load = [&](int j) { return make_ulonglong2(o[j], j < len ? tmp[j] : 0ull); };

@@ -35,7 +35,7 @@ using namespace divc;
 
 
 // mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw).
-constexpr int DIV_MAX_THREADS = 640;
+constexpr int DIV_MAX_THREADS = 576;
 
 __global__ void __launch_bounds__(DIV_MAX_THREADS)
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,

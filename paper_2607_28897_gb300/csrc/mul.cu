@@ -19,6 +19,16 @@ __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
                     Out + inst * (int64_t)nout, nout, smem);
 }
 
+template <int RB, int Q, int F>
+__global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
+    k_mul_kara(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
+               uint64_t *__restrict__ Out, int n) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int64_t inst = blockIdx.x;
+  blk_mul_kara<RB, Q, F, true>(A + inst * (int64_t)n, Bm + inst * (int64_t)n, n,
+                               Out + inst * (int64_t)(2 * n), smem);
+}
+
 // Threads per CTA for a product with `units` units of work: as few rounds as
 // the 1024-thread limit allows, then the smallest multiple of 32 that covers
 // the units in that many rounds.
@@ -50,23 +60,51 @@ static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, i
   const int optin = smem_optin();
   if (optin == 0) return BIGINT_ECUDA;
   if (smem > (size_t)optin) return BIGINT_EINVAL;
-  static bool configured = false;
-  if (!configured) {
+  static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
+  if (dyn_max < 0) {
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_mul<RB, Q, F, ASM, PP>));
     BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F, ASM, PP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    configured = true;
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes));
+    dyn_max = optin - (int)fa.sharedSizeBytes;
   }
+  if (smem > (size_t)dyn_max) return BIGINT_EINVAL;
   const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 640 : 1024);
   k_mul<RB, Q, F, ASM, PP><<<(unsigned)count, T, smem, st>>>(a, b, out, na, nb, nout);
   return bigint_launch_status();
 }
 
+template <int RB, int Q, int F>
+static int launch_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                       cudaStream_t st) {
+  const size_t smem = sizeof(uint32_t) * (size_t)blk_kara_smem_words<RB, Q>(n);
+  const int optin = smem_optin();
+  if (optin == 0) return BIGINT_ECUDA;
+  if (smem > (size_t)optin) return BIGINT_EINVAL;
+  static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
+  if (dyn_max < 0) {
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_mul_kara<RB, Q, F>));
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul_kara<RB, Q, F>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes));
+    dyn_max = optin - (int)fa.sharedSizeBytes;
+  }
+  if (smem > (size_t)dyn_max) return BIGINT_EINVAL;
+  const int T = pick_threads(blk_kara_units<RB, Q>(n), Q >= 16 ? 640 : 1024);
+  k_mul_kara<RB, Q, F><<<(unsigned)count, T, smem, st>>>(a, b, out, n);
+  return bigint_launch_status();
+}
+
 // Variant table (see bigint_set_variant).  Variant 0 picks by size from
 // measurements on GB300 (full-product sweep, 2^32-bit operand arrays):
-// ping-pong windows with 28-bit digits / 8-column chunks are fastest below
-// ~2^16 bits, with 29-bit digits / 16-column chunks above.
+// ping-pong windows with 28-bit digits / 8-column chunks below ~2^16 bits;
+// above, one level of Karatsuba over 28-bit / 8-column (2^17 bits) or
+// 29-bit / 16-column (2^18 bits and up) half products, and 29-bit /
+// 16-column schoolbook for products that are not square.
 static int g_mul_variant = 0;
-constexpr int MUL_VARIANTS = 10;
+constexpr int MUL_VARIANTS = 12;
 // Tuned variant per size class (class c: operands of [2^c, 2^(c+1)) limbs),
 // 0 = not tuned (built-in choice).  Written by bigint_tune_mul and
 // bigint_tuning_load.
@@ -92,8 +130,15 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
                int nb, int nout, cudaStream_t st) {
   int v = g_mul_variant;
   if (v == 0) v = g_mul_tuned[mul_size_class(na, nb)];
-  if (v == 0) v = (na > nb ? na : nb) < 1536 ? 9 : 8;
+  if (v == 0) {
+    const int nmax = na > nb ? na : nb;
+    v = nmax < 1536 ? 9 : (nmax < 3072 ? 11 : 10);  // 10, 11 fall back to 8 unless square
+  }
+  const bool square_full = na == nb && nout == na + nb && na >= 64;
+  if ((v == 10 || v == 11) && !square_full) v = 8;  // Karatsuba: square full products only
   switch (v) {
+    case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
+    case 11: return launch_kara<28, 8, 128>(a, b, out, count, na, st);
     case 2: return launch_variant<29, 8, 32>(a, b, out, count, na, nb, nout, st);
     case 3: return launch_variant<29, 4, 32>(a, b, out, count, na, nb, nout, st);
     case 4: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);

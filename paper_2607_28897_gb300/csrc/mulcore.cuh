@@ -309,4 +309,75 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
   return blk_addsub<false>(nout, 0u, load, store, scr);
 }
 
+// ---------------------------------------------------------------------------
+// One level of Karatsuba for a square product (both operands n limbs):
+// with x = x1 B^h + x0 and y = y1 B^h + y0 (h = floor(n/2)),
+//   x y = z2 B^(2h) + (z1 - z0 - z2) B^h + z0,
+//   z0 = x0 y0, z2 = x1 y1, z1 = (x0 + x1)(y0 + y1),
+// three half-size products (each by blk_mul) instead of four: 3/4 of the
+// digit products of the schoolbook full product.  Sec. VII names faster
+// multiplication as the next step after the quadratic one; this is its
+// exact-integer form.  The sums x0 + x1 and y0 + y1 are parked in the output
+// (free until z0 is written), z1 lives in shared memory.
+// smem: blk_kara_smem_words(n) words.  out: 2n limbs.
+// ---------------------------------------------------------------------------
+template <int RB, int Q>
+__host__ __device__ constexpr int blk_kara_smem_words(int n) {
+  const int hh = n - n / 2;
+  return 2 * (2 * hh + 2) + blk_mul_smem_words<RB, Q>(hh + 1, hh + 1);
+}
+
+template <int RB, int Q>
+__host__ __device__ constexpr int blk_kara_units(int n) {
+  const int hh = n - n / 2;
+  return blk_mul_units<RB, Q>(hh + 1, hh + 1);
+}
+
+template <int RB, int Q, int F, bool PP>
+__device__ void blk_mul_kara(const uint64_t *x, const uint64_t *y, int n, uint64_t *out,
+                             uint32_t *smem) {
+  const int h = n / 2, hh = n - h;  // x0, y0: h limbs; x1, y1: hh limbs
+  const int nz1 = 2 * hh + 2;
+  uint64_t *z1 = reinterpret_cast<uint64_t *>(smem);  // [nz1] limbs
+  uint32_t *msm = smem + 2 * nz1;                     // blk_mul's region
+  uint32_t *scr = msm;                                // scratch between products
+  uint64_t *s1 = out, *s2 = out + (hh + 1);
+  __shared__ uint32_t carries[2];
+  {  // s1 = x0 + x1, s2 = y0 + y1 (hh + 1 limbs each)
+    auto lx = [&](int j) { return make_ulonglong2(j < h ? x[j] : 0ull, x[h + j]); };
+    auto sx = [&](int j, uint64_t v) { s1[j] = v; };
+    const uint32_t c1 = blk_addsub<false>(hh, 0u, lx, sx, scr);
+    auto ly = [&](int j) { return make_ulonglong2(j < h ? y[j] : 0ull, y[h + j]); };
+    auto sy = [&](int j, uint64_t v) { s2[j] = v; };
+    const uint32_t c2 = blk_addsub<false>(hh, 0u, ly, sy, scr);
+    if (threadIdx.x == 0) {
+      carries[0] = c1;
+      carries[1] = c2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s1[hh] = carries[0];
+      s2[hh] = carries[1];
+    }
+    __syncthreads();
+  }
+  // z1 = s1 s2 (into shared memory)
+  blk_mul<RB, Q, F, false, PP>(s1, hh + 1, s2, hh + 1, z1, nz1, msm);
+  // z0 = x0 y0 -> out[0, 2h); z2 = x1 y1 -> out[2h, 2n)
+  blk_mul<RB, Q, F, false, PP>(x, h, y, h, out, 2 * h, msm);
+  blk_mul<RB, Q, F, false, PP>(x + h, hh, y + h, hh, out + 2 * h, 2 * hh, msm);
+  {  // z1 -= z0; z1 -= z2 (the difference x0 y1 + x1 y0 is nonnegative)
+    auto l0 = [&](int j) { return make_ulonglong2(z1[j], j < 2 * h ? out[j] : 0ull); };
+    auto st = [&](int j, uint64_t v) { z1[j] = v; };
+    blk_addsub<true>(nz1, 0u, l0, st, scr);
+    auto l2 = [&](int j) { return make_ulonglong2(z1[j], j < 2 * hh ? out[2 * h + j] : 0ull); };
+    blk_addsub<true>(nz1, 0u, l2, st, scr);
+  }
+  {  // out[h ..] += z1
+    auto la = [&](int j) { return make_ulonglong2(out[h + j], j < nz1 ? z1[j] : 0ull); };
+    auto sa = [&](int j, uint64_t v) { out[h + j] = v; };
+    blk_addsub<false>(2 * n - h, 0u, la, sa, scr);
+  }
+}
+
 }  // namespace bigint

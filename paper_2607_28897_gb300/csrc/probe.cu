@@ -78,12 +78,17 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
     }
 #pragma unroll
     for (int q = 0; q < 8; q++) y[q] += acc[q];
-  } else if constexpr (VARIANT == 5 || VARIANT == 6) {
-    // as 3 with the row digit made warp-uniform: 5 broadcasts it from lane
-    // 0 with a shuffle, 6 reads it from a warp-uniform shared address
-    __shared__ __align__(16) uint32_t srow[64];
-    if (threadIdx.x < 64) srow[threadIdx.x] = seed * threadIdx.x + 7;
-    __syncthreads();
+  } else if constexpr (VARIANT == 5) {
+    // as 0 (8 independent chains) in the C++ 64-bit multiply-add form
+#pragma unroll 1
+    for (int it = 0; it < PROBE_ITERS; it++) {
+#pragma unroll
+      for (int k = 0; k < 8; k++) y[k] += (uint64_t)x[k] * m;
+      x[it & 7] += (uint32_t)y[(it + 3) & 7];
+    }
+  } else if constexpr (VARIANT == 6) {
+    // sliding window, asm form, but the row digit differs per product (no
+    // operand reused between consecutive instructions)
     uint64_t acc[8];
     uint32_t W[16];
 #pragma unroll
@@ -92,21 +97,11 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
     for (int q = 0; q < 16; q++) W[q] = x[(q + 3) & 7] + q;
 #pragma unroll 1
     for (int it = 0; it < PROBE_ITERS / 8; it++) {
-      uint32_t av[8];
-      if constexpr (VARIANT == 5) {
-#pragma unroll
-        for (int t = 0; t < 8; t++) av[t] = __shfl_sync(FULL, x[t] ^ (uint32_t)it, 0);
-      } else {
-        const uint4 a0 = *reinterpret_cast<const uint4 *>(srow + ((it * 8) & 56));
-        const uint4 a1 = *reinterpret_cast<const uint4 *>(srow + ((it * 8) & 56) + 4);
-        av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
-        av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
-      }
 #pragma unroll
       for (int t = 0; t < 8; t++) {
 #pragma unroll
         for (int q = 0; q < 8; q++)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(av[t]), "r"(W[8 - t + q]));
+          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(x[(t + q) & 7]), "r"(W[8 - t + q]));
       }
 #pragma unroll
       for (int q = 0; q < 8; q++) W[8 + q] = W[q] + (uint32_t)it;
@@ -114,13 +109,13 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 #pragma unroll
     for (int q = 0; q < 8; q++) y[q] += acc[q];
   } else {
-    // as 0 with a per-thread (not warp-uniform) multiplier
-    const uint32_t mt = m ^ threadIdx.x;
+    // 8 independent chains, asm form, both multiplicands per-thread and
+    // different in every instruction
 #pragma unroll 1
     for (int it = 0; it < PROBE_ITERS; it++) {
 #pragma unroll
       for (int k = 0; k < 8; k++)
-        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(x[k]), "r"(mt));
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(x[k]), "r"(x[(k + 3) & 7]));
     }
   }
   __syncthreads();
@@ -133,7 +128,9 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 
 // Operations per thread for one probe launch.
 static double probe_ops_per_thread(int variant) {
-  if (variant >= 3 && variant <= 6) return (double)(PROBE_ITERS / 8) * 64;
+  if (variant == 3 || variant == 4) return (double)(PROBE_ITERS / 8) * 64;
+  if (variant == 5 || variant == 7) return (double)PROBE_ITERS * 8;
+  if (variant == 6) return (double)(PROBE_ITERS / 8) * 64;
   return (double)PROBE_ITERS * 8;
 }
 

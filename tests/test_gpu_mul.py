@@ -85,3 +85,23 @@ def test_config_sweep_full_size(bi, orc, n):
     k = 8 if n >= 4096 else 16
     idx = np.unique(np.concatenate([[0, a.shape[0] - 1], rng.choice(a.shape[0], k)]))
     assert np.array_equal(p[idx], orc.batch_mul(a[idx], b[idx]))
+
+
+@pytest.mark.parametrize("variant", range(1, 12))
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 511, 1000, 2049])
+def test_every_variant(bi, orc, variant, n):
+    """Every multiply variant (digit size, chunk width, window form,
+    Karatsuba) gives the oracle's product; Karatsuba variants fall back to
+    the schoolbook kernel below 64 limbs."""
+    from paper_2607_28897_gb300 import inputs
+
+    a = inputs.limbs(700 + n, 3, n)
+    b = inputs.limbs(800 + n, 3, n)
+    ones = np.full((1, n), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    a, b = np.concatenate([a, ones]), np.concatenate([b, ones])
+    bi.set_variant(0, variant)
+    try:
+        p = to_host(bi.mul(to_dev(a), to_dev(b)))
+    finally:
+        bi.set_variant(0, 0)
+    assert np.array_equal(p, orc.batch_mul(a, b))
