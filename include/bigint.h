@@ -233,6 +233,11 @@ int bigint_tuning_load(const char *path);
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 
+/* The multiply variant (1..11) a full na x nb product runs with the current
+ * settings (default choice, tuning table, fallbacks), so that measurements
+ * can count the digit products of the algorithm actually used. */
+int bigint_mul_variant_for(int32_t na, int32_t nb);
+
 /* Integer-pipe throughput probe used for the multiply roofline: every SM
  * runs a register-only loop of one instruction form at full occupancy and
  * times itself with the SM cycle counter.  Returns thread-level operations

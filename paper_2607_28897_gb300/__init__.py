@@ -57,6 +57,7 @@ SIGNATURES = {
     "bigint_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
     "bigint_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
     "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -258,6 +259,11 @@ def shinv(v, h: int, nw: int, w=None, status=None, workspace=None, stream=None):
 def set_variant(op: int, variant: int) -> None:
     """Select the kernel variant of an operation (op 0 = multiply)."""
     _check(load().bigint_set_variant(op, variant), "bigint_set_variant")
+
+
+def mul_variant_for(na: int, nb: int) -> int:
+    """The multiply variant a full na x nb product runs with (1..11)."""
+    return int(load().bigint_mul_variant_for(na, nb))
 
 
 def probe_int_throughput(variant: int):

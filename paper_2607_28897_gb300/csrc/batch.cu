@@ -54,7 +54,7 @@ __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uin
       return 0;
     case BIGINT_OP_DIVMOD: {
       const int nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
-      return divmod_one(in + o.a, o.na, in + o.b, o.nb, out + o.o1, nq, out + o.o2, ws, smem,
+      return divmod_one<DRB, DQ, DF>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, nq, out + o.o2, ws, smem,
                         smem_words, scr);
     }
     default:

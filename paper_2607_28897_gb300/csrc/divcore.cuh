@@ -10,7 +10,11 @@ namespace bigint {
 namespace divc {
 namespace {  // internal linkage: this header is included by several units
 
-constexpr int DRB = 29, DQ = 16, DF = 32;  // product variant used inside division
+// Product variants used inside division: DRB/DQ/DF for large operands,
+// SRB/SQ/SF below DIV_SMALL_LIMBS (measured faster there on GB300).
+constexpr int DRB = 29, DQ = 16, DF = 32;
+constexpr int SRB = 28, SQ = 8, SF = 128;
+constexpr int DIV_SMALL_LIMBS = 2048;
 constexpr int MAX_CORRECTIONS = 8;
 
 // ---------------------------------------------------------------------------
@@ -118,6 +122,7 @@ __device__ Work carve(uint64_t *base, int nu, int nv, int h) {
 // shared-memory budget, otherwise a sum of slice products, each added into
 // place (out must not overlap x, y or tmp).  Writes out[0..nout).
 // ---------------------------------------------------------------------------
+template <int RB, int Q, int F>
 __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
                         int nout, uint64_t *tmp, uint32_t *smem, int smem_words) {
   if (nx <= 0 || ny <= 0) {
@@ -125,13 +130,13 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
     __syncthreads();
     return;
   }
-  if (blk_mul_smem_words<DRB, DQ>(nx, ny) <= smem_words) {
-    blk_mul<DRB, DQ, DF, false, true>(x, nx, y, ny, out, nout, smem);
+  if (blk_mul_smem_words<RB, Q>(nx, ny) <= smem_words) {
+    blk_mul<RB, Q, F, false, true>(x, nx, y, ny, out, nout, smem);
     return;
   }
   // slice both operands into pieces of s limbs whose products fit
   int s = 8192;
-  while (s > 64 && blk_mul_smem_words<DRB, DQ>(s, s) > smem_words) s -= 64;
+  while (s > 64 && blk_mul_smem_words<RB, Q>(s, s) > smem_words) s -= 64;
   uint32_t *scr = smem;  // blk_addsub scratch (the slice product is done)
   blk_zero(out, nout);
   __syncthreads();
@@ -142,7 +147,7 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
       const int off = i0 + j0;
       if (off >= nout) continue;
       const int len = sx + sy;
-      blk_mul<DRB, DQ, DF, false, true>(x + i0, sx, y + j0, sy, tmp, len, smem);
+      blk_mul<RB, Q, F, false, true>(x + i0, sx, y + j0, sy, tmp, len, smem);
       const int n = nout - off;
       uint64_t *o = out + off;
       auto load = [&](int j) { return make_ulonglong2(o[j], j < len ? tmp[j] : 0ull); };
@@ -185,12 +190,13 @@ __device__ void newton_start(const uint64_t *v, int k, int l, uint64_t *w, int c
 // floor for d >= 0, ceiling for d < 0.  w is in W.w (prec nw), the result
 // goes to W.wn and the two buffers are swapped.  Returns prec(w').
 // ---------------------------------------------------------------------------
+template <int RB, int Q, int F>
 __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, int nw,
                            uint32_t *smem, int smem_words, uint32_t *scr) {
   const int e = hp - m;
   // P1 = vt * w
   const int n1 = nvt + nw;
-  mul_any(vt, nvt, W.w, nw, W.p, n1, W.tmp, smem, smem_words);
+  mul_any<RB, Q, F>(vt, nvt, W.w, nw, W.p, n1, W.tmp, smem, smem_words);
   const int pp = blk_prec(W.p, n1, scr);
   const bool neg = pp > e;  // vt w >= B^e (d <= 0; d = 0 gives y = 0 either way)
   // D = |B^e - P1|
@@ -215,7 +221,7 @@ __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, 
   const int n2 = nw + nd;
   uint32_t cin = 0;
   if (nd > 0) {
-    mul_any(W.w, nw, W.d, nd, W.p, n2, W.tmp, smem, smem_words);
+    mul_any<RB, Q, F>(W.w, nw, W.d, nd, W.p, n2, W.tmp, smem, smem_words);
     if (neg) cin = (uint32_t)blk_any_nonzero(W.p, s < n2 ? s : n2, scr);  // ceiling
   }
   const uint64_t *Y = W.p + s;
@@ -241,6 +247,7 @@ __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, 
 
 // w ~ B^h / v (0 <= B^h/v - w < 2 before the final correction); returns
 // prec(w).  v has precision k+1.
+template <int RB, int Q, int F>
 __device__ int shinv_newton(const uint64_t *v, int k, int h, Work &W, uint32_t *smem,
                             int smem_words, uint32_t *scr) {
   const int L = h - k;
@@ -250,7 +257,7 @@ __device__ int shinv_newton(const uint64_t *v, int k, int h, Work &W, uint32_t *
   while (l < L) {
     const int m = (l - 2 < L - l) ? l - 2 : L - l;
     const int t = (k < l + m + 2) ? k : l + m + 2;
-    nw = newton_step(t + l + m, m, v + (k - t), t + 1, W, nw, smem, smem_words, scr);
+    nw = newton_step<RB, Q, F>(t + l + m, m, v + (k - t), t + 1, W, nw, smem, smem_words, scr);
     l += m;
   }
   return nw;
@@ -304,6 +311,7 @@ __device__ int correct(const uint64_t *v, int kv, uint64_t *R, uint64_t *Qh, int
 // modulo B^(k+2), exact correction.  ws: this instance's workspace region of
 // ws_limbs(nu, nv, nu) limbs.  Returns the status (0, EDIVZERO, ERANGE,
 // EINTERNAL).
+template <int RB, int Q, int F>
 __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q,
                           int nq, uint64_t *r, uint64_t *ws, uint32_t *smem, int smem_words,
                           uint32_t *scr) {
@@ -325,10 +333,10 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
     return BIGINT_OK;
   }
   const int h = ku;
-  int nw = shinv_newton(v, k, h, W, smem, smem_words, scr);
+  int nw = shinv_newton<RB, Q, F>(v, k, h, W, smem, smem_words, scr);
   // q^ = floor(u w / B^h)
   const int nz = ku + nw;
-  mul_any(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words);
+  mul_any<RB, Q, F>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words);
   const int nqh = nz - h > 0 ? nz - h : 0;
   const int qcap = nqh + 1 < W.cap_w ? nqh + 1 : W.cap_w;
   for (int j = threadIdx.x; j < qcap; j += blockDim.x) W.qh[j] = j < nqh ? W.p[h + j] : 0;
@@ -336,7 +344,7 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
   const int pq = blk_prec(W.qh, qcap, scr);
   // r^ = (u - q^ v) mod B^(kv+1): the low kv+1 limbs of q^ v only
   if (pq > 0) {
-    mul_any(W.qh, pq, v, kv, W.p, kv + 1, W.tmp, smem, smem_words);
+    mul_any<RB, Q, F>(W.qh, pq, v, kv, W.p, kv + 1, W.tmp, smem, smem_words);
   } else {
     blk_zero(W.p, kv + 1);
     __syncthreads();

@@ -37,6 +37,7 @@ using namespace divc;
 // mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw).
 constexpr int DIV_MAX_THREADS = 576;
 
+template <int RB, int Q, int F>
 __global__ void __launch_bounds__(DIV_MAX_THREADS)
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,
              uint64_t *Ro, int32_t *status, int nu, int nv, int nq, int mode, int h_arg,
@@ -62,9 +63,9 @@ __global__ void __launch_bounds__(DIV_MAX_THREADS)
   if (mode == 1) {
     // ---- shifted inverse: w = floor(B^h / v), h = h_arg >= nv >= kv
     const int h = h_arg;
-    int nw = shinv_newton(v, k, h, W, smem, smem_words, scr);
+    int nw = shinv_newton<RB, Q, F>(v, k, h, W, smem, smem_words, scr);
     // R = (B^h - v w) mod B^(kv+1), then exact correction of w
-    mul_any(v, kv, W.w, nw, W.p, kv + 1, W.tmp, smem, smem_words);
+    mul_any<RB, Q, F>(v, kv, W.w, nw, W.p, kv + 1, W.tmp, smem, smem_words);
     {
       uint64_t *P = W.p, *R = W.r;
       auto load = [&](int j) { return make_ulonglong2(j == h ? 1ull : 0ull, P[j]); };
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(DIV_MAX_THREADS)
   }
 
   // ---- division
-  st = divmod_one(U + inst * (int64_t)nu, nu, v, nv, q, nq, Ro + inst * (int64_t)nv,
+  st = divmod_one<RB, Q, F>(U + inst * (int64_t)nu, nu, v, nv, q, nq, Ro + inst * (int64_t)nv,
                   ws + inst * ws_stride, smem, smem_words, scr);
   if (status && threadIdx.x == 0) status[inst] = st;
 }
@@ -107,36 +108,47 @@ size_t shinv_workspace(int64_t count, int nv, int h) {
   return (size_t)count * (size_t)ws_limbs(nv, nv, h) * sizeof(uint64_t);
 }
 
-static int launch_div_common(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
-                             int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
-                             int h, void *ws, cudaStream_t st) {
+template <int RB, int Q, int F>
+static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                              int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
+                              int h, void *ws, cudaStream_t st) {
   const int optin = div_smem_optin();
   if (optin == 0) return BIGINT_ECUDA;
-  const int static_bytes = BLK_SCRATCH_WORDS * 4;
-  int smem_words = (optin - static_bytes) / 4;
+  static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
+  if (dyn_max < 0) {
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_divmod<RB, Q, F>));
+    dyn_max = optin - (int)fa.sharedSizeBytes;
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_divmod<RB, Q, F>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+  }
+  int smem_words = dyn_max / 4;
   // the largest product a division performs is about (2 H) x H limbs;
   // ask for no more shared memory than one such product needs
   const int H = (mode == 0 ? nu : h);
-  const int need = blk_mul_smem_words<DRB, DQ>(H, H);
+  const int need = blk_mul_smem_words<RB, Q>(H, H);
   if (need < smem_words) smem_words = need;
-  const int units = blk_mul_units<DRB, DQ>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
+  const int units = blk_mul_units<RB, Q>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
   int T = (units + DIV_MAX_THREADS - 1) / DIV_MAX_THREADS;
   T = (units + T - 1) / T;
   T = (T + 31) / 32 * 32;
   if (T < 64) T = 64;
   if (T > DIV_MAX_THREADS) T = DIV_MAX_THREADS;
-  static bool configured = false;
-  if (!configured) {
-    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_divmod, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         optin - static_bytes));
-    configured = true;
-  }
   const int hcap = mode == 0 ? nu : h;
   const int64_t stride = ws_limbs(nu, nv, hcap);
-  k_divmod<<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
+  k_divmod<RB, Q, F><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
       u, v, q, r, status, nu, nv, nq, mode, h, reinterpret_cast<uint64_t *>(ws), stride,
       smem_words);
   return bigint_launch_status();
+}
+
+static int launch_div_common(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                             int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
+                             int h, void *ws, cudaStream_t st) {
+  const int H = (mode == 0 ? nu : h);
+  if (H < DIV_SMALL_LIMBS)
+    return launch_div_variant<SRB, SQ, SF>(u, v, q, r, status, count, nu, nv, nq, mode, h, ws, st);
+  return launch_div_variant<DRB, DQ, DF>(u, v, q, r, status, count, nu, nv, nq, mode, h, ws, st);
 }
 
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,

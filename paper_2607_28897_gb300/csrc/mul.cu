@@ -126,8 +126,8 @@ int mul_set_variant(int v) {
 // Largest square operand (limbs) whose product fits one CTA's shared memory.
 int mul_max_limbs() { return BIGINT_MUL_MAX_LIMBS; }
 
-int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
-               int nb, int nout, cudaStream_t st) {
+// The variant a call with these shapes runs (after defaults and fallbacks).
+int mul_variant_for(int na, int nb, int nout) {
   int v = g_mul_variant;
   if (v == 0) v = g_mul_tuned[mul_size_class(na, nb)];
   if (v == 0) {
@@ -136,6 +136,12 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
   }
   const bool square_full = na == nb && nout == na + nb && na >= 64;
   if ((v == 10 || v == 11) && !square_full) v = 8;  // Karatsuba: square full products only
+  return v;
+}
+
+int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+               int nb, int nout, cudaStream_t st) {
+  const int v = mul_variant_for(na, nb, nout);
   switch (v) {
     case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
     case 11: return launch_kara<28, 8, 128>(a, b, out, count, na, st);
