@@ -275,7 +275,7 @@ def main():
     import torch
 
     import paper_2607_28897_gb300 as bi
-    from paper_2607_28897_gb300 import inputs
+    from paper_2607_28897_gb300 import inputs, ranks
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -289,7 +289,7 @@ def main():
     sizes = [int(s) for s in args.sizes.split(",")]
 
     # ---- inputs, resident in HBM before timing (seeded, per rank)
-    seed_off = 1000 * rank
+    seed_off = ranks.rank_seed(0, rank)
     sweep = {}
     for n in sizes:
         a, b = inputs.config_sweep_torch(n, seed=2 + seed_off, device=dev)
@@ -373,11 +373,7 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = ranks.max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ops = step_units(sizes)
     limb_ops_step = sum(b * u for _, b, u in ops)
     value = world * limb_ops_step * args.steps / (ms_total * 1e-3) / 1e9
@@ -537,11 +533,9 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    from paper_2607_28897_gb300 import ranks
+
+    dt = ranks.max_over_ranks(time.perf_counter() - t0, dist, dev)
     return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
 
