@@ -34,7 +34,7 @@ static_assert(sizeof(OpDev) == sizeof(bigint_op), "descriptor layout");
 
 // Product variant used by batch kernels (both operands in shared memory).
 constexpr int BRB = 29, BQ = 16, BF = 32;
-constexpr int BATCH_MAX_THREADS = 640;
+constexpr int BATCH_MAX_THREADS = 512;
 
 __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uint64_t *out,
                                          uint64_t *ws, uint32_t *smem, int smem_words,
@@ -50,7 +50,7 @@ __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uin
                                    : (int)blk_addsub<true>(o.na, 0u, load, store, scr);
     }
     case BIGINT_OP_MUL:
-      blk_mul<BRB, BQ, BF, false, true>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, o.na + o.nb, smem);
+      blk_mul_call<BRB, BQ, BF>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, o.na + o.nb, smem, 0);
       return 0;
     case BIGINT_OP_DIVMOD: {
       const int nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;

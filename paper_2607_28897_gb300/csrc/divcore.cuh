@@ -124,14 +124,14 @@ __device__ Work carve(uint64_t *base, int nu, int nv, int h) {
 // ---------------------------------------------------------------------------
 template <int RB, int Q, int F>
 __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
-                        int nout, uint64_t *tmp, uint32_t *smem, int smem_words) {
+                        int nout, uint64_t *tmp, uint32_t *smem, int smem_words, int lo = 0) {
   if (nx <= 0 || ny <= 0) {
     blk_zero(out, nout);
     __syncthreads();
     return;
   }
   if (blk_mul_smem_words<RB, Q>(nx, ny) <= smem_words) {
-    blk_mul<RB, Q, F, false, true>(x, nx, y, ny, out, nout, smem);
+    blk_mul_call<RB, Q, F>(x, nx, y, ny, out, nout, smem, lo);
     return;
   }
   // slice both operands into pieces of s limbs whose products fit
@@ -146,8 +146,9 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
       const int sy = ny - j0 < s ? ny - j0 : s;
       const int off = i0 + j0;
       if (off >= nout) continue;
-      const int len = sx + sy;
-      blk_mul<RB, Q, F, false, true>(x + i0, sx, y + j0, sy, tmp, len, smem);
+      if (lo > 0 && off + sx + sy + 1 <= lo) continue;  // entirely below the band
+      const int len = sx + sy < nout - off ? sx + sy : nout - off;
+      blk_mul_call<RB, Q, F>(x + i0, sx, y + j0, sy, tmp, len, smem, lo > off ? lo - off : 0);
       const int n = nout - off;
       uint64_t *o = out + off;
       auto load = [&](int j) { return make_ulonglong2(o[j], j < len ? tmp[j] : 0ull); };
@@ -193,26 +194,24 @@ __device__ void newton_start(const uint64_t *v, int k, int l, uint64_t *w, int c
 template <int RB, int Q, int F>
 __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, int nw,
                            uint32_t *smem, int smem_words, uint32_t *scr) {
-  const int e = hp - m;
-  // P1 = vt * w
-  const int n1 = nvt + nw;
-  mul_any<RB, Q, F>(vt, nvt, W.w, nw, W.p, n1, W.tmp, smem, smem_words);
-  const int pp = blk_prec(W.p, n1, scr);
-  const bool neg = pp > e;  // vt w >= B^e (d <= 0; d = 0 gives y = 0 either way)
-  // D = |B^e - P1|
-  int nd;
+  // d = B^e - vt w is small: |d| < 2 vt < B^(t+2) / 2 (t = nvt - 1, the
+  // iterate is within two units), and e = t + l >= t + 2.  So d is fixed by
+  // vt w modulo B^(t+2) -- the powDiff product "performed modulo a power of
+  // the base" of Fig. 6 -- and its sign is the top bit of that residue:
+  // L = (-d) mod B^(t+2) is below B^(t+2)/2 exactly when d <= 0.
+  const int nl = nvt + 1;
+  mul_any<RB, Q, F>(vt, nvt, W.w, nw, W.p, nl, W.tmp, smem, smem_words);
+  const bool neg = (W.p[nl - 1] >> 63) == 0;  // d <= 0: vt w >= B^e
+  int nd = nl;
   {
     uint64_t *P = W.p, *D = W.d;
-    if (!neg) {  // B^e - P1 over e limbs (P1 < B^e, P1 > 0)
-      auto load = [&](int j) { return make_ulonglong2(0ull, j < n1 ? P[j] : 0ull); };
-      auto store = [&](int j, uint64_t x) { D[j] = x; };
-      blk_addsub<true>(e, 0u, load, store, scr);
-      nd = e;
-    } else {  // P1 - B^e over pp limbs
-      auto load = [&](int j) { return make_ulonglong2(P[j], j == e ? 1ull : 0ull); };
-      auto store = [&](int j, uint64_t x) { D[j] = x; };
-      blk_addsub<true>(pp, 0u, load, store, scr);
-      nd = pp;
+    auto store = [&](int j, uint64_t x) { D[j] = x; };
+    if (neg) {  // |d| = L
+      auto load = [&](int j) { return make_ulonglong2(P[j], 0ull); };
+      blk_addsub<false>(nl, 0u, load, store, scr);
+    } else {  // |d| = B^(t+2) - L
+      auto load = [&](int j) { return make_ulonglong2(0ull, P[j]); };
+      blk_addsub<true>(nl, 0u, load, store, scr);
     }
   }
   nd = blk_prec(W.d, nd, scr);
@@ -334,9 +333,11 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
   }
   const int h = ku;
   int nw = shinv_newton<RB, Q, F>(v, k, h, W, smem, smem_words, scr);
-  // q^ = floor(u w / B^h)
+  // q^ = floor(u w / B^h), from a product that may drop the columns below
+  // limb h - 2: q^ is then at most a few units low, which the final
+  // correction absorbs (it is never high, since w <= B^h / v)
   const int nz = ku + nw;
-  mul_any<RB, Q, F>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words);
+  mul_any<RB, Q, F>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words, h > 2 ? h - 2 : 0);
   const int nqh = nz - h > 0 ? nz - h : 0;
   const int qcap = nqh + 1 < W.cap_w ? nqh + 1 : W.cap_w;
   for (int j = threadIdx.x; j < qcap; j += blockDim.x) W.qh[j] = j < nqh ? W.p[h + j] : 0;

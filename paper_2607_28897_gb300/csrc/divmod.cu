@@ -35,10 +35,13 @@ using namespace divc;
 
 
 // mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw).
-constexpr int DIV_MAX_THREADS = 576;
+// Thread cap per product variant: 512 gives the wide-chunk variant 128
+// registers (no spills in its products); the small variant keeps a 640 cap,
+// whose 96-register budget fits two blocks of ~320 threads on one SM.
+template <int Q> constexpr int div_max_threads() { return Q >= 16 ? 512 : 640; }
 
 template <int RB, int Q, int F>
-__global__ void __launch_bounds__(DIV_MAX_THREADS)
+__global__ void __launch_bounds__(div_max_threads<Q>())
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,
              uint64_t *Ro, int32_t *status, int nu, int nv, int nq, int mode, int h_arg,
              uint64_t *ws, int64_t ws_stride, int smem_words) {
@@ -129,11 +132,12 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
   const int need = blk_mul_smem_words<RB, Q>(H, H);
   if (need < smem_words) smem_words = need;
   const int units = blk_mul_units<RB, Q>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
-  int T = (units + DIV_MAX_THREADS - 1) / DIV_MAX_THREADS;
+  constexpr int TMAX = div_max_threads<Q>();
+  int T = (units + TMAX - 1) / TMAX;
   T = (units + T - 1) / T;
   T = (T + 31) / 32 * 32;
   if (T < 64) T = 64;
-  if (T > DIV_MAX_THREADS) T = DIV_MAX_THREADS;
+  if (T > TMAX) T = TMAX;
   const int hcap = mode == 0 ? nu : h;
   const int64_t stride = ws_limbs(nu, nv, hcap);
   k_divmod<RB, Q, F><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(

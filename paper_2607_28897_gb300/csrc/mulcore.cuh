@@ -166,27 +166,43 @@ __device__ __forceinline__ void load_q(uint32_t (&r)[Q], const uint32_t *p) {
   }
 }
 
-// conv_unit with ping-pong window buffers (see row_steps_pp).
-template <int RB, int Q, int F>
+// conv_unit with ping-pong window buffers (see row_steps_pp).  Band limits:
+// a chunk that starts at or above output bit 64 nout contributes nothing to
+// out[0, nout) and is skipped (exact); with lo > 0 a chunk whose digits and
+// overflow word all lie below bit 64 lo is skipped too, which drops its
+// contribution -- callers that pass lo > 0 only use limbs well above lo and
+// correct the result afterwards.
+template <int RB, int Q, int F, bool BAND>
 __device__ __forceinline__ void conv_unit_pp(int u, int KR, int KW, const uint32_t *sRow,
                                              const uint32_t *sW, uint64_t *out, int nout,
-                                             uint64_t *sH) {
+                                             uint64_t *sH, int lo) {
   static_assert(F % Q == 0, "flush interval must be a whole number of groups");
   static_assert(F < (1 << (64 - 2 * RB)), "flush interval too long for this digit size");
   constexpr int FG = F / Q;
+  constexpr int64_t CB = (int64_t)RB * Q;  // bits per chunk
   const int NWp = KW * Q;
   const bool pair = u < KR;
+  auto skip_chunk = [&](int c) {
+    if constexpr (!BAND) return false;
+    const int64_t b0 = CB * c;
+    return b0 >= 64 * (int64_t)nout || b0 + CB + 64 <= 64 * (int64_t)lo;
+  };
+  const bool f_skip = skip_chunk(u);
+  const bool m_skip = pair ? skip_chunk(KW + u) : true;
+  if (f_skip && (!pair || m_skip)) return;
   const int switch_g = pair ? u + 1 : -1;
+  const int g_begin = (pair && f_skip) ? u + 1 : 0;
+  const int g_end = (pair && m_skip) ? u : KR;
   uint64_t acc[Q], X = 0;
   uint32_t A[Q], Bf[Q];
 #pragma unroll
   for (int q = 0; q < Q; q++) acc[q] = 0;
-  load_q<Q>(A, sW + u * Q);  // hi half of group 0
-  bool fwd = true;
+  if (g_begin == 0) load_q<Q>(A, sW + u * Q);  // hi half of group 0
+  bool fwd = g_begin == 0;
   // one group: hi/lo are the buffer roles for this group's parity
   auto group = [&](int g, uint32_t (&hi)[Q], uint32_t (&lo)[Q]) {
     if (g == switch_g) {  // low chunk done: continue with its partner
-      finish_chunk<RB, Q>(acc, X, u, out, nout, sH);
+      if (!f_skip) finish_chunk<RB, Q>(acc, X, u, out, nout, sH);
 #pragma unroll
       for (int q = 0; q < Q; q++) { acc[q] = 0; hi[q] = 0; }  // window[NWp..) is padding
       X = 0;
@@ -198,14 +214,21 @@ __device__ __forceinline__ void conv_unit_pp(int u, int KR, int KW, const uint32
     row_steps_pp<Q, 0>(acc, lo, hi, sRow + i0);
     if ((g + 1) % FG == 0) normalise<RB, Q>(acc, X);
   };
-  int g = 0;
+  // The first group of the range always takes hi = A: A holds the window's
+  // high half of group 0, or is zeroed at the switch when the range starts
+  // with the partner chunk.
+  int g = g_begin;
 #pragma unroll 1
-  for (; g + 1 <= KR; g += 2) {
+  for (; g + 1 <= g_end; g += 2) {
     group(g, A, Bf);      // hi = A, lo = B
     group(g + 1, Bf, A);  // hi = B (the previous lo), lo = A
   }
-  if (g <= KR) group(g, A, Bf);
-  finish_chunk<RB, Q>(acc, X, pair ? KW + u : u, out, nout, sH);
+  if (g <= g_end) group(g, A, Bf);
+  if (g_end == KR) {
+    if (!pair || !m_skip) finish_chunk<RB, Q>(acc, X, pair ? KW + u : u, out, nout, sH);
+  } else if (!f_skip) {
+    finish_chunk<RB, Q>(acc, X, u, out, nout, sH);  // partner chunk skipped
+  }
 }
 
 template <int RB, int Q, int F, bool ASM>
@@ -255,12 +278,15 @@ __device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t 
 }
 
 // Low nout limbs of x[0..nx) * y[0..ny) into out[0..nout) (out must not
-// overlap x or y).  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
+// overlap x or y).  With BAND (which needs PP), chunks at or above limb nout
+// are skipped, and lo > 0 allows the result to miss the products of chunks
+// below limb lo (see conv_unit_pp): limbs >= lo + 2 are then at most a few
+// units of limb lo below the exact value.  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
 // aligned.  Returns the carry out of limb nout-1 of the final addition
 // (0 whenever nout >= nx + ny).
-template <int RB, int Q, int F, bool ASM = false, bool PP = false>
+template <int RB, int Q, int F, bool ASM = false, bool PP = false, bool BAND = false>
 __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
-                            int nout, uint32_t *smem) {
+                            int nout, uint32_t *smem, int lo = 0) {
   const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
   const bool x_is_row = NX <= NY;
   const uint32_t *rw = reinterpret_cast<const uint32_t *>(x_is_row ? x : y);
@@ -283,7 +309,7 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
 
   // ---- A3: convolution, one unit at a time per thread
   for (int u = t; u < KW; u += T) {
-    if constexpr (PP) conv_unit_pp<RB, Q, F>(u, KR, KW, sRow, sW, out, nout, sH);
+    if constexpr (PP) conv_unit_pp<RB, Q, F, BAND>(u, KR, KW, sRow, sW, out, nout, sH, lo);
     else conv_unit<RB, Q, F, ASM>(u, KR, KW, sRow, sW, out, nout, sH);
   }
   __syncthreads();
@@ -307,6 +333,17 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
   };
   auto store = [&](int j, uint64_t v) { out[j] = v; };
   return blk_addsub<false>(nout, 0u, load, store, scr);
+}
+
+// blk_mul (band-limited) as one out-of-line function: the division and batch
+// kernels call products from many places, and one shared copy keeps their
+// code (and register pressure) small; the call costs nothing next to a
+// product.
+template <int RB, int Q, int F>
+__device__ __noinline__ uint32_t blk_mul_call(const uint64_t *x, int nx, const uint64_t *y,
+                                              int ny, uint64_t *out, int nout, uint32_t *smem,
+                                              int lo) {
+  return blk_mul<RB, Q, F, false, true, true>(x, nx, y, ny, out, nout, smem, lo);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,7 +86,7 @@ int tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
 int tune_batch(bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status, void *ws,
                size_t bytes, cudaStream_t st, int *best_threads) {
   if (bytes < batch_workspace_bytes(B)) return BIGINT_ENOMEM;
-  static const int cand[] = {256, 384, 512, 640};
+  static const int cand[] = {256, 384, 512};
   int best = 0;
   float best_ms = 1e30f;
   for (int T : cand) {
