@@ -230,10 +230,24 @@ int bigint_tuning_load(const char *path);
  *   variants 10, 11: one level of Karatsuba (square full products of at
  *   least 64 limbs; otherwise variant 8) over half products of variant 8,
  *   resp. variant 9
+ *   variant 12: the tensor-core product -- the digit convolution of the
+ *   schoolbook product (Sec. V-B) as fp16 matrix products (tcgen05.mma)
+ *   over signed base-256 digits with exact fp32 accumulation; bit-identical
+ *   results.  Needs the shorter operand to fit shared memory (about 10700
+ *   limbs; otherwise variant 8).  One persistent CTA per SM, which holds
+ *   all of the SM's tensor memory while it runs.
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 
-/* The multiply variant (1..11) a full na x nb product runs with the current
+/* BIGINT_ETIMEOUT if a tensor-core product stopped at one of its device
+ * wait limits (about one second per wait; its outputs are then undefined)
+ * since the previous call, else BIGINT_OK.  Synchronises the device and
+ * clears the record.  The paper has no counterpart: the waits exist only in
+ * the tensor-core schedule, which hands work between threads and the
+ * tensor cores through shared-memory barriers.                              */
+int bigint_check_timeout(void);
+
+/* The multiply variant (1..12) a full na x nb product runs with the current
  * settings (default choice, tuning table, fallbacks), so that measurements
  * can count the digit products of the algorithm actually used. */
 int bigint_mul_variant_for(int32_t na, int32_t nb);

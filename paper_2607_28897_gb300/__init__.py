@@ -58,6 +58,7 @@ SIGNATURES = {
     "bigint_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
+    "bigint_check_timeout": ([], ctypes.c_int),
     "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -262,8 +263,14 @@ def set_variant(op: int, variant: int) -> None:
 
 
 def mul_variant_for(na: int, nb: int) -> int:
-    """The multiply variant a full na x nb product runs with (1..11)."""
+    """The multiply variant a full na x nb product runs with (1..12)."""
     return int(load().bigint_mul_variant_for(na, nb))
+
+
+def check_timeout() -> None:
+    """Raises BigIntError if a tensor-core product stopped at a device wait
+    limit since the previous check (synchronises the device)."""
+    _check(load().bigint_check_timeout(), "bigint_check_timeout")
 
 
 def probe_int_throughput(variant: int):

@@ -14,6 +14,7 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
 int mul_max_limbs();
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
+int tc_take_timeout();
 int probe_int_throughput(int variant, double *ops, double *mhz);
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                   int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
@@ -178,6 +179,8 @@ int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);
   return BIGINT_EINVAL;
 }
+
+int bigint_check_timeout(void) { return tc_take_timeout(); }
 
 int bigint_mul_variant_for(int32_t na, int32_t nb) {
   if (na < 1 || nb < 1) return BIGINT_EINVAL;

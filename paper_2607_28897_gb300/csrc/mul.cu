@@ -103,8 +103,12 @@ static int launch_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int6
 // above, one level of Karatsuba over 28-bit / 8-column (2^17 bits) or
 // 29-bit / 16-column (2^18 bits and up) half products, and 29-bit /
 // 16-column schoolbook for products that are not square.
+size_t mul_tc_smem(int na, int nb);
+int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+                  int nb, int nout, cudaStream_t st);
+
 static int g_mul_variant = 0;
-constexpr int MUL_VARIANTS = 12;
+constexpr int MUL_VARIANTS = 13;
 // Tuned variant per size class (class c: operands of [2^c, 2^(c+1)) limbs),
 // 0 = not tuned (built-in choice).  Written by bigint_tune_mul and
 // bigint_tuning_load.
@@ -136,6 +140,7 @@ int mul_variant_for(int na, int nb, int nout) {
   }
   const bool square_full = na == nb && nout == na + nb && na >= 64;
   if ((v == 10 || v == 11) && !square_full) v = 8;  // Karatsuba: square full products only
+  if (v == 12 && mul_tc_smem(na, nb) == 0) v = 8;    // tensor-core product: shared memory bound
   return v;
 }
 
@@ -143,6 +148,7 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
                int nb, int nout, cudaStream_t st) {
   const int v = mul_variant_for(na, nb, nout);
   switch (v) {
+    case 12: return launch_mul_tc(a, b, out, count, na, nb, nout, st);
     case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
     case 11: return launch_kara<28, 8, 128>(a, b, out, count, na, st);
     case 2: return launch_variant<29, 8, 32>(a, b, out, count, na, nb, nout, st);
