@@ -190,17 +190,18 @@ def cpu_model() -> str:
 # --------------------------------------------------------------------------
 # committed ncu traffic of the multiply kernel, valid only for its source
 # --------------------------------------------------------------------------
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=("tcmul.cu", "mul.cu", "blockops.cuh", "common.cuh")) -> str:
     h = hashlib.sha256()
-    for f in ("mulcore.cuh", "mul.cu", "blockops.cuh", "common.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2607_28897_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic():
-    """key = value lines of profiles/mul_traffic.txt (DRAM bytes per k_mul
-    launch from an ncu capture), or None once the kernel source changed."""
-    path = os.path.join(ROOT, "profiles", "mul_traffic.txt")
+    """key = value lines of profiles/mul_tc_traffic.txt (DRAM bytes per
+    multiply launch from an ncu capture), or None once the kernel source
+    changed."""
+    path = os.path.join(ROOT, "profiles", "mul_tc_traffic.txt")
     d = {}
     try:
         for line in open(path):
@@ -410,15 +411,18 @@ def main():
 
     # ---- roofline of the dominant kernel: the multiply launch at the largest
     #      size (2^19 bits), the longest launch of the step
-    ipc, probe_mhz = bi.probe_int_throughput(0)  # IMAD.WIDE per SM per clock
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = clk["sm_mhz"] if clk else probe_mhz
-    peak = ipc * sms * mhz * 1e6 / 1e12  # T IMAD.WIDE / s at the clock under load
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
     nmax = max(sizes)
+    vmax = bi.mul_variant_for(nmax, nmax)
 
     def mul_units(n):
         """Limb products the multiply algorithm the library picks performs
-        for one n x n product (Karatsuba: three (n/2+1)-limb half products)."""
+        for one n x n product (Karatsuba: three (n/2+1)-limb half products;
+        the tensor-core product is a schoolbook product)."""
         v = bi.mul_variant_for(n, n)
         if v in (10, 11):
             hh = n - n // 2
@@ -426,26 +430,48 @@ def main():
         return n * n
 
     mul_ms = breakdown[f"mul_{nmax}"]["ms"]
-    mul_work = 4.0 * sweep_batch(nmax) * mul_units(nmax)  # 4 IMAD.WIDE per limb product
-    achieved = mul_work / (mul_ms * 1e-3) / 1e12
     all_ms = sum(breakdown[f"mul_{n}"]["ms"] for n in sizes)
-    all_work = sum(4.0 * sweep_batch(n) * mul_units(n) for n in sizes)
     tr = committed_traffic()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T IMAD.WIDE-equivalent/s (4 per limb product)", "frac": achieved / peak,
-                "traffic": tr.get(f"bytes_per_launch_{nmax}") if tr else None,
-                "kernel": (f"{'k_mul_kara' if bi.mul_variant_for(nmax, nmax) in (10, 11) else 'k_mul'}"
-                           f" (variant {bi.mul_variant_for(nmax, nmax)}), {nmax}-limb operands, "
-                           f"batch {sweep_batch(nmax)}"),
-                "algorithmic_work": "4 IMAD.WIDE-equivalents per limb product the algorithm performs",
-                "frac_all_sizes": all_work / (all_ms * 1e-3) / 1e12 / peak,
-                "peak_basis": (f"measured {ipc:.1f} IMAD.WIDE/clk/SM x {sms} SMs x "
-                               f"{mhz:.0f} MHz (median SM clock in the timed region)")}
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    kernel = (f"{'k_mul_tc<256>' if vmax == 12 else 'k_mul_kara' if vmax in (10, 11) else 'k_mul'}"
+              f" (variant {vmax}), {nmax}-limb operands, batch {sweep_batch(nmax)}")
+    if vmax == 12:
+        # tensor bound: 2 flops per fp16 digit product of the 8-bit schoolbook
+        # convolution, (8 n)^2 per n x n product; sustained peak because the
+        # kernel is timed inside the long step
+        def tc_flops(n):
+            return 2.0 * (8 * n) ** 2 * sweep_batch(n)
+
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        achieved = tc_flops(nmax) / (mul_ms * 1e-3) / 1e12
+        tc_sizes = [n for n in sizes if bi.mul_variant_for(n, n) == 12]
+        tc_ms = sum(breakdown[f"mul_{n}"]["ms"] for n in tc_sizes)
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": tr.get(f"bytes_per_launch_{nmax}") if tr else None,
+                    "kernel": kernel,
+                    "algorithmic_work": "2 x (8 n)^2 flops per n x n product: fp16 products of "
+                                        "base-256 digits, accumulated in fp32",
+                    "frac_all_sizes": (sum(tc_flops(n) for n in tc_sizes) / (tc_ms * 1e-3) / 1e12
+                                       / peak) if tc_sizes else None,
+                    "peak_basis": ("of measured: MEASURED_PEAKS.json bf16_tflops_sustained "
+                                   "(fp16 and bf16 share the nominal dense rate)")
+                    if "bf16_tflops_sustained" in peaks else "of fallback: 1700 TFLOP/s sustained"}
+    else:
+        ipc, probe_mhz = bi.probe_int_throughput(0)  # IMAD.WIDE per SM per clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk["sm_mhz"] if clk else probe_mhz
+        peak = ipc * sms * mhz * 1e6 / 1e12  # T IMAD.WIDE / s at the clock under load
+        mul_work = 4.0 * sweep_batch(nmax) * mul_units(nmax)  # 4 IMAD.WIDE per limb product
+        achieved = mul_work / (mul_ms * 1e-3) / 1e12
+        all_work = sum(4.0 * sweep_batch(n) * mul_units(n) for n in sizes)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "T IMAD.WIDE-equivalent/s (4 per limb product)",
+                    "frac": achieved / peak, "traffic": None, "kernel": kernel,
+                    "algorithmic_work": "4 IMAD.WIDE-equivalents per limb product the algorithm "
+                                        "performs",
+                    "frac_all_sizes": all_work / (all_ms * 1e-3) / 1e12 / peak,
+                    "peak_basis": (f"measured {ipc:.1f} IMAD.WIDE/clk/SM x {sms} SMs x "
+                                   f"{mhz:.0f} MHz (median SM clock in the timed region)")}
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     add_bytes = sum(24.0 * sweep_batch(n) * n for n in sizes)
     add_ms = sum(breakdown[f"add_{n}"]["ms"] for n in sizes)

@@ -98,14 +98,19 @@ static int launch_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int6
 }
 
 // Variant table (see bigint_set_variant).  Variant 0 picks by size from
-// measurements on GB300 (full-product sweep, 2^32-bit operand arrays):
-// ping-pong windows with 28-bit digits / 8-column chunks below ~2^16 bits;
-// above, one level of Karatsuba over 28-bit / 8-column (2^17 bits) or
-// 29-bit / 16-column (2^18 bits and up) half products, and 29-bit /
-// 16-column schoolbook for products that are not square.
+// measurements on GB300 (full-product sweep, 2^32-bit operand arrays): the
+// tensor-core product (tcmul.cu) once the shorter operand has TC_MIN_LIMBS
+// limbs and fits shared memory; otherwise ping-pong windows with 28-bit
+// digits / 8-column chunks below ~2^16 bits; above, one level of Karatsuba
+// over 28-bit / 8-column (2^17 bits) or 29-bit / 16-column (2^18 bits and
+// up) half products, and 29-bit / 16-column schoolbook for products that
+// are not square.
 size_t mul_tc_smem(int na, int nb);
 int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                   int nb, int nout, cudaStream_t st);
+
+// Shorter operand (limbs) from which the default is the tensor-core product.
+constexpr int TC_MIN_LIMBS = 256;
 
 static int g_mul_variant = 0;
 constexpr int MUL_VARIANTS = 13;
@@ -135,8 +140,11 @@ int mul_variant_for(int na, int nb, int nout) {
   int v = g_mul_variant;
   if (v == 0) v = g_mul_tuned[mul_size_class(na, nb)];
   if (v == 0) {
-    const int nmax = na > nb ? na : nb;
-    v = nmax < 1536 ? 9 : (nmax < 3072 ? 11 : 10);  // 10, 11 fall back to 8 unless square
+    const int nmax = na > nb ? na : nb, nmin = na < nb ? na : nb;
+    if (nmin >= TC_MIN_LIMBS && mul_tc_smem(na, nb) > 0)
+      v = 12;
+    else
+      v = nmax < 1536 ? 9 : (nmax < 3072 ? 11 : 10);  // 10, 11 fall back to 8 unless square
   }
   const bool square_full = na == nb && nout == na + nb && na >= 64;
   if ((v == 10 || v == 11) && !square_full) v = 8;  // Karatsuba: square full products only
