@@ -29,8 +29,11 @@
 //    offsets both 128 bytes reads the whole 128 x 128 Toeplitz block from
 //    31 such 128-byte core matrices (a group of G blocks needs 16 G + 15).
 //  * Exactness.  Each accumulator sums at most G x 128 products between
-//    drains (|sum| <= G * 2^21 = 2^23 for G = 4: integers below 2^24 are
-//    exact in fp32 and in the tensor core's fp32 accumulation), then is
+//    drains: every partial sum is an integer of magnitude at most
+//    G * 2^21 <= 2^24 (G = 8), and all integers up to 2^24 are exact in fp32
+//    and in the tensor core's fp32 accumulation (the byte pattern 0x7F80...
+//    makes every digit +-128 and every product of a column the same sign,
+//    reaching 2^24 exactly; it is a parity case).  The accumulator is then
 //    converted exactly (cvt.rni) and added to int32 column sums in
 //    registers; a column sum is at most (8 n + 1) * 2^14 < 2^31 for
 //    n <= 16383 limbs.
@@ -42,8 +45,10 @@
 //    subtracted at the end with one more borrow scan.
 //
 // Schedule: a persistent CTA of 2 NT threads loops over instances; per
-// instance over tiles of NT output columns; per tile over groups of G = 4
-// Toeplitz blocks.  Thread 0 issues a group's MMAs into one of two NT-column
+// instance over tiles of NT output columns; per tile over groups of G = 8
+// Toeplitz blocks (G = 4 when the longer Hankel buffers do not fit).  Fewer,
+// larger groups matter: every drain reads the whole accumulator out of
+// tensor memory, and the drains do not fully overlap the MMAs.  Thread 0 issues a group's MMAs into one of two NT-column
 // fp32 accumulators in tensor memory and commits them to an mbarrier; while
 // they run, all threads build the next group's Hankel core matrices (double
 // buffered) and drain the other accumulator.  NT = 256 (one CTA per SM, all
@@ -59,8 +64,9 @@
 namespace bigint {
 namespace tcm {
 
-constexpr int G = 4;             // Toeplitz blocks per accumulation group
-constexpr int HB = 16 * G + 15;  // Hankel core matrices per group buffer
+// G: Toeplitz blocks per accumulation group; a group's Hankel buffer holds
+// 16 G + 15 core matrices.
+__host__ __device__ constexpr int hankel_blocks(int G) { return 16 * G + 15; }
 constexpr int ZB = 18;           // zero core matrices (operand of the clearing MMA)
 // NT: output columns per tile (= MMA N at most); 2 NT threads, 2 NT TMEM
 // columns (two accumulators).
@@ -80,8 +86,9 @@ struct Layout {
   uint32_t xs, z, h0, h1, cs, his, total;  // byte offsets in dynamic shared memory
 };
 
-template <int NT>
+template <int NT, int G>
 __host__ __device__ inline Layout layout(int nx, int ny) {
+  constexpr int HB = hankel_blocks(G);
   Layout L;
   L.mx = (8 * nx + 1 + 127) / 128;
   L.ey = (8 * ny + 127) / 128;
@@ -240,7 +247,9 @@ __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, i
 
 // Hankel core matrices of the group whose last block is eb: matrix j, row r,
 // element w = recoded y digit at 128 eb + 127 - 8 j - r - w.
+template <int G>
 __device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, int eb) {
+  constexpr int HB = hankel_blocks(G);
   const int64_t ytop = 128ll * eb + 127;
   for (int row = threadIdx.x; row < HB * 8; row += blockDim.x) {
     const int j = row >> 3, r = row & 7;
@@ -283,10 +292,16 @@ __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t 
                 IDESC_M128 | ((uint32_t)(W >> 3) << 17), 0);
       }
     }
+    // K steps of 16 digits: A moves by 2 core matrices (256 bytes), B by two
+    // leading offsets; the start-address field is bits 0-13 (address >> 4)
+    uint64_t da = sdesc(aa, 128, 128), db = sdesc(ba, lbo_b, 128);
+    const uint64_t step_b = (2u * lbo_b) >> 4;
 #pragma unroll
-    for (int s = 0; s < 8; s++)
-      mma_f16(dtm + (uint32_t)lo, sdesc(aa + 256u * s, 128, 128),
-              sdesc(ba + 2u * s * lbo_b, lbo_b, 128), id, s == 0 ? accf : 1u);
+    for (int s = 0; s < 8; s++) {
+      mma_f16(dtm + (uint32_t)lo, da, db, id, s == 0 ? accf : 1u);
+      da += 16;
+      db += step_b;
+    }
   }
   mma_commit(mbar);
 }
@@ -307,7 +322,7 @@ __device__ __forceinline__ void drain(uint32_t taddr, int cq, int W, int (&acc)[
   }
 }
 
-template <int NT>
+template <int NT, int G>
 __global__ void __launch_bounds__(2 * NT, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
              uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count) {
@@ -319,7 +334,7 @@ __global__ void __launch_bounds__(2 * NT, 256 / NT)
   __shared__ uint32_t s_carry[2];  // high word of the previous tile's last limb, carry
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Layout Ly = layout<NT>(nx, ny);
+  const Layout Ly = layout<NT, G>(nx, ny);
   const uint32_t sbase = smem_u32(sm);
   const uint32_t xs_a = sbase + Ly.xs, z_a = sbase + Ly.z;
   const uint32_t lbo_b = (uint32_t)Ly.ptot * 16u;
@@ -369,7 +384,7 @@ __global__ void __launch_bounds__(2 * NT, 256 / NT)
 #pragma unroll
       for (int i = 0; i < 64; i++) acc[i] = 0;
       if (NG > 0) {
-        build_h(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi);
+        build_h<G>(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi);
         fence_async_smem();
         __syncthreads();
         bool bad = false;
@@ -389,7 +404,7 @@ __global__ void __launch_bounds__(2 * NT, 256 / NT)
           }
           if (gi + 1 < NG) {
             const int na = ea + G, nb2 = na + G - 1 < e_hi ? na + G - 1 : e_hi;
-            build_h(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2);
+            build_h<G>(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2);
           }
           tc_fence_before();
           fence_async_smem();
@@ -477,7 +492,7 @@ __global__ void __launch_bounds__(2 * NT, 256 / NT)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <int NT>
+template <int NT, int G>
 static int tc_dyn_max() {
   static int dyn = -1;
   if (dyn < 0) {
@@ -487,10 +502,10 @@ static int tc_dyn_max() {
         cudaSuccess)
       return 0;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G>) != cudaSuccess) return 0;
     const int d = optin - (int)fa.sharedSizeBytes;
-    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, d) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             d) != cudaSuccess)
       return 0;
     dyn = d;
   }
@@ -504,11 +519,20 @@ static int tc_tile(int nx, int ny) {
   return (8 * nx + 1 + 127) / 128 + (8 * ny + 127) / 128 <= 128 ? 128 : 256;
 }
 
-template <int NT>
+template <int NT, int G>
 static size_t tc_smem(int nx, int ny) {
-  const tcm::Layout L = tcm::layout<NT>(nx, ny);
-  const int d = tc_dyn_max<NT>();
+  const tcm::Layout L = tcm::layout<NT, G>(nx, ny);
+  const int d = tc_dyn_max<NT, G>();
   return d > 0 && L.total <= (uint32_t)d ? L.total : 0;
+}
+
+// Group size: 8 Toeplitz blocks per drain where the Hankel buffers fit,
+// else 4 (0: the product does not fit at all).
+template <int NT>
+static int tc_group(int nx, int ny) {
+  if (tc_smem<NT, 8>(nx, ny)) return 8;
+  if (tc_smem<NT, 4>(nx, ny)) return 4;
+  return 0;
 }
 
 // Dynamic shared memory the tensor-core product of an na x nb product
@@ -516,13 +540,15 @@ static size_t tc_smem(int nx, int ny) {
 size_t mul_tc_smem(int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
   if (nx < 1 || ny > 16383) return 0;
-  return tc_tile(nx, ny) == 128 ? tc_smem<128>(nx, ny) : tc_smem<256>(nx, ny);
+  if (tc_tile(nx, ny) == 128)
+    return tc_group<128>(nx, ny) == 8 ? tc_smem<128, 8>(nx, ny) : tc_smem<128, 4>(nx, ny);
+  return tc_group<256>(nx, ny) == 8 ? tc_smem<256, 8>(nx, ny) : tc_smem<256, 4>(nx, ny);
 }
 
-template <int NT>
+template <int NT, int G>
 static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_t count, int nx,
                      int ny, int nout, cudaStream_t st) {
-  const size_t smem = tc_smem<NT>(nx, ny);
+  const size_t smem = tc_smem<NT, G>(nx, ny);
   if (smem == 0) return BIGINT_EINVAL;
   if (count == 0) return BIGINT_OK;
   int dev = 0, sms = 0;
@@ -530,7 +556,7 @@ static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_
   BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t slots = (int64_t)sms * (256 / NT);  // CTAs resident at once
   const int64_t grid = count < slots ? count : slots;
-  tcm::k_mul_tc<NT><<<(unsigned)grid, 2 * NT, smem, st>>>(x, y, out, nx, ny, nout, count);
+  tcm::k_mul_tc<NT, G><<<(unsigned)grid, 2 * NT, smem, st>>>(x, y, out, nx, ny, nout, count);
   return bigint_launch_status();
 }
 
@@ -540,8 +566,11 @@ int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
   int nx = na, ny = nb;
   if (nb < na) { x = b; y = a; nx = nb; ny = na; }
   if (nx < 1 || ny > 16383 || nout < 1 || nout > na + nb) return BIGINT_EINVAL;
-  return tc_tile(nx, ny) == 128 ? launch_tc<128>(x, y, out, count, nx, ny, nout, st)
-                                : launch_tc<256>(x, y, out, count, nx, ny, nout, st);
+  if (tc_tile(nx, ny) == 128)
+    return tc_group<128>(nx, ny) == 8 ? launch_tc<128, 8>(x, y, out, count, nx, ny, nout, st)
+                                      : launch_tc<128, 4>(x, y, out, count, nx, ny, nout, st);
+  return tc_group<256>(nx, ny) == 8 ? launch_tc<256, 8>(x, y, out, count, nx, ny, nout, st)
+                                    : launch_tc<256, 4>(x, y, out, count, nx, ny, nout, st);
 }
 
 // BIGINT_ETIMEOUT if a tensor-core product hit a wait limit since the last
