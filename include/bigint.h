@@ -236,12 +236,20 @@ int bigint_tuning_load(const char *path);
  *   results.  Needs the shorter operand to fit shared memory (about 10700
  *   limbs; otherwise variant 8).  One persistent CTA per SM, which holds
  *   all of the SM's tensor memory while it runs.
+ * op 1 = division (divmod and shinv):
+ *   variant 0 (default) or 1: operands of 2048 limbs and more run in a
+ *   kernel that holds its SM's tensor memory and computes products whose
+ *   shorter operand has at least 256 limbs on the tensor cores (as variant
+ *   12 of the multiply); smaller divisions use the integer products
+ *   variant 2: integer products (blk_mul) for every division
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 
-/* BIGINT_ETIMEOUT if a tensor-core product stopped at one of its device
- * wait limits (about one second per wait; its outputs are then undefined)
- * since the previous call, else BIGINT_OK.  Synchronises the device and
+/* BIGINT_ETIMEOUT if a tensor-core product (multiply variant 12 or a
+ * division's tensor-core product) stopped at one of its device wait limits
+ * (about one second per wait; its outputs are then undefined, and a
+ * division reports BIGINT_ETIMEOUT in its status) since the previous call,
+ * else BIGINT_OK.  Synchronises the device and
  * clears the record.  The paper has no counterpart: the waits exist only in
  * the tensor-core schedule, which hands work between threads and the
  * tensor cores through shared-memory barriers.                              */

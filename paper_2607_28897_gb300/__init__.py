@@ -258,7 +258,8 @@ def shinv(v, h: int, nw: int, w=None, status=None, workspace=None, stream=None):
 
 
 def set_variant(op: int, variant: int) -> None:
-    """Select the kernel variant of an operation (op 0 = multiply)."""
+    """Select the kernel variant of an operation (op 0 = multiply, op 1 =
+    division; see bigint_set_variant in include/bigint.h)."""
     _check(load().bigint_set_variant(op, variant), "bigint_set_variant")
 
 

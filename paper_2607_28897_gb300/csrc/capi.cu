@@ -15,6 +15,8 @@ int mul_max_limbs();
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
+int div_take_timeout();
+int div_set_variant(int v);
 int probe_int_throughput(int variant, double *ops, double *mhz);
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                   int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
@@ -177,10 +179,15 @@ int bigint_tuning_load(const char *path) { return path ? tuning_load(path) : BIG
 
 int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);
+  if (op == 1) return div_set_variant(variant);
   return BIGINT_EINVAL;
 }
 
-int bigint_check_timeout(void) { return tc_take_timeout(); }
+int bigint_check_timeout(void) {
+  const int a = tc_take_timeout(), b = div_take_timeout();
+  if (a == BIGINT_ECUDA || b == BIGINT_ECUDA) return BIGINT_ECUDA;
+  return a != BIGINT_OK ? a : b;
+}
 
 int bigint_mul_variant_for(int32_t na, int32_t nb) {
   if (na < 1 || nb < 1) return BIGINT_EINVAL;

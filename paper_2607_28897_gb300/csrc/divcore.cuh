@@ -5,6 +5,7 @@
 #pragma once
 #include "blockops.cuh"
 #include "mulcore.cuh"
+#include "tccore.cuh"
 
 namespace bigint {
 namespace divc {
@@ -16,6 +17,9 @@ constexpr int DRB = 29, DQ = 16, DF = 32;
 constexpr int SRB = 28, SQ = 8, SF = 128;
 constexpr int DIV_SMALL_LIMBS = 2048;
 constexpr int MAX_CORRECTIONS = 8;
+// Products whose shorter operand has at least this many limbs run on the
+// tensor cores in the division kernels that hold tensor memory (TC = true).
+constexpr int TC_DIV_MIN = 256;
 
 // ---------------------------------------------------------------------------
 // One-thread long division for the Newton start value (tiny operands:
@@ -118,17 +122,57 @@ __device__ Work carve(uint64_t *base, int nu, int nv, int h) {
 }
 
 // ---------------------------------------------------------------------------
-// Product of arbitrary (limb) sizes: one blk_mul when both operands fit the
-// shared-memory budget, otherwise a sum of slice products, each added into
-// place (out must not overlap x, y or tmp).  Writes out[0..nout).
+// Tensor-core product inside a division kernel of 512 threads holding 512
+// TMEM columns (tccore.cuh), as one out-of-line copy.
 // ---------------------------------------------------------------------------
-template <int RB, int Q, int F>
+template <int G>
+__device__ __noinline__ bool tc_call(tcm::TcCtx *c, const uint64_t *x, int nx, const uint64_t *y,
+                                     int ny, uint64_t *out, int nout, int lo) {
+  return tcm::tc_product<256, G>(*c, x, nx, y, ny, out, nout, lo);
+}
+
+// out[0..nout) = x * y on the tensor cores when the shorter operand has
+// TC_DIV_MIN limbs and the product's layout fits smem_words; false (nothing
+// written) otherwise.  With lo > 0 the tensor-core band semantics apply
+// (tc_product): limbs >= lo + 2 are exact or one unit of limb lo + 2 high,
+// limbs below the first computed tile are not written.
+__device__ __forceinline__ bool tc_mul(tcm::TcCtx *tc, const uint64_t *x, int nx,
+                                       const uint64_t *y, int ny, uint64_t *out, int nout,
+                                       int smem_words, int lo) {
+  const int ns = nx < ny ? nx : ny, nl = nx < ny ? ny : nx;
+  if (tc == nullptr || tc->aborted || ns < TC_DIV_MIN) return false;
+  const uint64_t *xs = nx <= ny ? x : y, *ys = nx <= ny ? y : x;
+  const int no = nout < nx + ny ? nout : nx + ny;
+  const uint32_t bytes = 4u * (uint32_t)smem_words;
+  if (tcm::layout<256, 8>(ns, nl).total <= bytes)
+    tc_call<8>(tc, xs, ns, ys, nl, out, no, lo);
+  else if (tcm::layout<256, 4>(ns, nl).total <= bytes)
+    tc_call<4>(tc, xs, ns, ys, nl, out, no, lo);
+  else
+    return false;
+  for (int j = no + (int)threadIdx.x; j < nout; j += blockDim.x) out[j] = 0;
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Product of arbitrary (limb) sizes: on the tensor cores (TC, large
+// operands), else one blk_mul when both operands fit the shared-memory
+// budget, otherwise a sum of slice products, each added into place (out
+// must not overlap x, y or tmp).  Writes out[0..nout) (band mode: see
+// blk_mul and tc_mul).
+// ---------------------------------------------------------------------------
+template <int RB, int Q, int F, bool TC = false>
 __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
-                        int nout, uint64_t *tmp, uint32_t *smem, int smem_words, int lo = 0) {
+                        int nout, uint64_t *tmp, uint32_t *smem, int smem_words, int lo = 0,
+                        tcm::TcCtx *tc = nullptr) {
   if (nx <= 0 || ny <= 0) {
     blk_zero(out, nout);
     __syncthreads();
     return;
+  }
+  if constexpr (TC) {
+    if (tc_mul(tc, x, nx, y, ny, out, nout, smem_words, lo)) return;
   }
   if (blk_mul_smem_words<RB, Q>(nx, ny) <= smem_words) {
     blk_mul_call<RB, Q, F>(x, nx, y, ny, out, nout, smem, lo);
@@ -191,16 +235,17 @@ __device__ void newton_start(const uint64_t *v, int k, int l, uint64_t *w, int c
 // floor for d >= 0, ceiling for d < 0.  w is in W.w (prec nw), the result
 // goes to W.wn and the two buffers are swapped.  Returns prec(w').
 // ---------------------------------------------------------------------------
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool TC = false>
 __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, int nw,
-                           uint32_t *smem, int smem_words, uint32_t *scr) {
+                           uint32_t *smem, int smem_words, uint32_t *scr,
+                           tcm::TcCtx *tc = nullptr) {
   // d = B^e - vt w is small: |d| < 2 vt < B^(t+2) / 2 (t = nvt - 1, the
   // iterate is within two units), and e = t + l >= t + 2.  So d is fixed by
   // vt w modulo B^(t+2) -- the powDiff product "performed modulo a power of
   // the base" of Fig. 6 -- and its sign is the top bit of that residue:
   // L = (-d) mod B^(t+2) is below B^(t+2)/2 exactly when d <= 0.
   const int nl = nvt + 1;
-  mul_any<RB, Q, F>(vt, nvt, W.w, nw, W.p, nl, W.tmp, smem, smem_words);
+  mul_any<RB, Q, F, TC>(vt, nvt, W.w, nw, W.p, nl, W.tmp, smem, smem_words, 0, tc);
   const bool neg = (W.p[nl - 1] >> 63) == 0;  // d <= 0: vt w >= B^e
   int nd = nl;
   {
@@ -220,7 +265,7 @@ __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, 
   const int n2 = nw + nd;
   uint32_t cin = 0;
   if (nd > 0) {
-    mul_any<RB, Q, F>(W.w, nw, W.d, nd, W.p, n2, W.tmp, smem, smem_words);
+    mul_any<RB, Q, F, TC>(W.w, nw, W.d, nd, W.p, n2, W.tmp, smem, smem_words, 0, tc);
     if (neg) cin = (uint32_t)blk_any_nonzero(W.p, s < n2 ? s : n2, scr);  // ceiling
   }
   const uint64_t *Y = W.p + s;
@@ -246,9 +291,9 @@ __device__ int newton_step(int hp, int m, const uint64_t *vt, int nvt, Work &W, 
 
 // w ~ B^h / v (0 <= B^h/v - w < 2 before the final correction); returns
 // prec(w).  v has precision k+1.
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool TC = false>
 __device__ int shinv_newton(const uint64_t *v, int k, int h, Work &W, uint32_t *smem,
-                            int smem_words, uint32_t *scr) {
+                            int smem_words, uint32_t *scr, tcm::TcCtx *tc = nullptr) {
   const int L = h - k;
   int l = L < 3 ? L : 3;
   newton_start(v, k, l, W.w, W.cap_w);
@@ -256,7 +301,8 @@ __device__ int shinv_newton(const uint64_t *v, int k, int h, Work &W, uint32_t *
   while (l < L) {
     const int m = (l - 2 < L - l) ? l - 2 : L - l;
     const int t = (k < l + m + 2) ? k : l + m + 2;
-    nw = newton_step<RB, Q, F>(t + l + m, m, v + (k - t), t + 1, W, nw, smem, smem_words, scr);
+    nw = newton_step<RB, Q, F, TC>(t + l + m, m, v + (k - t), t + 1, W, nw, smem, smem_words,
+                                   scr, tc);
     l += m;
   }
   return nw;
@@ -310,10 +356,10 @@ __device__ int correct(const uint64_t *v, int kv, uint64_t *R, uint64_t *Qh, int
 // modulo B^(k+2), exact correction.  ws: this instance's workspace region of
 // ws_limbs(nu, nv, nu) limbs.  Returns the status (0, EDIVZERO, ERANGE,
 // EINTERNAL).
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool TC = false>
 __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q,
                           int nq, uint64_t *r, uint64_t *ws, uint32_t *smem, int smem_words,
-                          uint32_t *scr) {
+                          uint32_t *scr, tcm::TcCtx *tc = nullptr) {
   Work W = carve(ws, nu, nv, nu);
   int st = BIGINT_OK;
   const int kv = blk_prec(v, nv, scr);
@@ -332,12 +378,16 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
     return BIGINT_OK;
   }
   const int h = ku;
-  int nw = shinv_newton<RB, Q, F>(v, k, h, W, smem, smem_words, scr);
+  int nw = shinv_newton<RB, Q, F, TC>(v, k, h, W, smem, smem_words, scr, tc);
   // q^ = floor(u w / B^h), from a product that may drop the columns below
-  // limb h - 2: q^ is then at most a few units low, which the final
-  // correction absorbs (it is never high, since w <= B^h / v)
+  // limb h - 2: q^ is then at most a few units low (integer product: it is
+  // never high, since w <= B^h / v) or one unit high (tensor-core product,
+  // whose band mode adds a margin above the dropped columns); the final
+  // correction absorbs either.  u w + B^h < B^(ku + nw) since h = ku, so
+  // the banded value never wraps.
   const int nz = ku + nw;
-  mul_any<RB, Q, F>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words, h > 2 ? h - 2 : 0);
+  mul_any<RB, Q, F, TC>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words, h > 2 ? h - 2 : 0,
+                        tc);
   const int nqh = nz - h > 0 ? nz - h : 0;
   const int qcap = nqh + 1 < W.cap_w ? nqh + 1 : W.cap_w;
   for (int j = threadIdx.x; j < qcap; j += blockDim.x) W.qh[j] = j < nqh ? W.p[h + j] : 0;
@@ -345,7 +395,7 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
   const int pq = blk_prec(W.qh, qcap, scr);
   // r^ = (u - q^ v) mod B^(kv+1): the low kv+1 limbs of q^ v only
   if (pq > 0) {
-    mul_any<RB, Q, F>(W.qh, pq, v, kv, W.p, kv + 1, W.tmp, smem, smem_words);
+    mul_any<RB, Q, F, TC>(W.qh, pq, v, kv, W.p, kv + 1, W.tmp, smem, smem_words, 0, tc);
   } else {
     blk_zero(W.p, kv + 1);
     __syncthreads();

@@ -37,64 +37,107 @@ using namespace divc;
 // mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw).
 // Thread cap per product variant: 512 gives the wide-chunk variant 128
 // registers (no spills in its products); the small variant keeps a 640 cap,
-// whose 96-register budget fits two blocks of ~320 threads on one SM.
-template <int Q> constexpr int div_max_threads() { return Q >= 16 ? 512 : 640; }
+// whose 96-register budget fits two blocks of ~320 threads on one SM.  The
+// tensor-core variant (TC) runs exactly 512 threads and holds all 512 TMEM
+// columns of its SM: products with a shorter operand of TC_DIV_MIN limbs or
+// more run on the tensor cores (tccore.cuh), smaller ones on blk_mul.
+template <int Q, bool TC> constexpr int div_max_threads() {
+  return TC ? 512 : (Q >= 16 ? 512 : 640);
+}
 
-template <int RB, int Q, int F>
-__global__ void __launch_bounds__(div_max_threads<Q>())
+template <int RB, int Q, int F, bool TC>
+__global__ void __launch_bounds__(div_max_threads<Q, TC>())
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,
              uint64_t *Ro, int32_t *status, int nu, int nv, int nq, int mode, int h_arg,
              uint64_t *ws, int64_t ws_stride, int smem_words) {
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(1024) uint32_t smem[];
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  __shared__ tcm::TcShared tsh;
   const int64_t inst = blockIdx.x;
   const uint64_t *v = V + inst * (int64_t)nv;
   uint64_t *q = Qo + inst * (int64_t)nq;
   const int hcap = mode == 0 ? nu : h_arg;
   Work W = carve(ws + inst * ws_stride, nu, nv, hcap);
   int st = BIGINT_OK;
-
-  const int kv = blk_prec(v, nv, scr);
-  if (kv == 0) {  // division by zero: q = r = 0
-    blk_zero(q, nq);
-    if (mode == 0) blk_zero(Ro + inst * (int64_t)nv, nv);
-    if (status && threadIdx.x == 0) status[inst] = BIGINT_EDIVZERO;
-    return;
+  tcm::TcCtx tcc;
+  tcm::TcCtx *tc = nullptr;
+  if constexpr (TC) {
+    tcm::tc_init<256>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
+    tc = &tcc;
   }
-  const int k = kv - 1;
 
-  if (mode == 1) {
-    // ---- shifted inverse: w = floor(B^h / v), h = h_arg >= nv >= kv
-    const int h = h_arg;
-    int nw = shinv_newton<RB, Q, F>(v, k, h, W, smem, smem_words, scr);
-    // R = (B^h - v w) mod B^(kv+1), then exact correction of w
-    mul_any<RB, Q, F>(v, kv, W.w, nw, W.p, kv + 1, W.tmp, smem, smem_words);
-    {
-      uint64_t *P = W.p, *R = W.r;
-      auto load = [&](int j) { return make_ulonglong2(j == h ? 1ull : 0ull, P[j]); };
-      auto store = [&](int j, uint64_t x) { R[j] = x; };
-      blk_addsub<true>(kv + 1, 0u, load, store, scr);
+  [&] {
+    const int kv = blk_prec(v, nv, scr);
+    if (kv == 0) {  // division by zero: q = r = 0
+      blk_zero(q, nq);
+      if (mode == 0) blk_zero(Ro + inst * (int64_t)nv, nv);
+      st = BIGINT_EDIVZERO;
+      return;
     }
-    // w may grow by one limb in the correction
-    for (int j = threadIdx.x + nw; j < W.cap_w; j += blockDim.x) W.w[j] = 0;
-    st = correct(v, kv, W.r, W.w, nw + 1 < W.cap_w ? nw + 1 : W.cap_w, scr);
-    __syncthreads();
-    const int pw = blk_prec(W.w, W.cap_w, scr);
-    if (pw > nq && st == BIGINT_OK) st = BIGINT_ERANGE;
-    for (int j = threadIdx.x; j < nq; j += blockDim.x) q[j] = j < W.cap_w ? W.w[j] : 0;
-    if (status && threadIdx.x == 0) status[inst] = st;
-    return;
-  }
+    const int k = kv - 1;
 
-  // ---- division
-  st = divmod_one<RB, Q, F>(U + inst * (int64_t)nu, nu, v, nv, q, nq, Ro + inst * (int64_t)nv,
-                  ws + inst * ws_stride, smem, smem_words, scr);
+    if (mode == 1) {
+      // ---- shifted inverse: w = floor(B^h / v), h = h_arg >= nv >= kv
+      const int h = h_arg;
+      int nw = shinv_newton<RB, Q, F, TC>(v, k, h, W, smem, smem_words, scr, tc);
+      // R = (B^h - v w) mod B^(kv+1), then exact correction of w
+      mul_any<RB, Q, F, TC>(v, kv, W.w, nw, W.p, kv + 1, W.tmp, smem, smem_words, 0, tc);
+      {
+        uint64_t *P = W.p, *R = W.r;
+        auto load = [&](int j) { return make_ulonglong2(j == h ? 1ull : 0ull, P[j]); };
+        auto store = [&](int j, uint64_t x) { R[j] = x; };
+        blk_addsub<true>(kv + 1, 0u, load, store, scr);
+      }
+      // w may grow by one limb in the correction
+      for (int j = threadIdx.x + nw; j < W.cap_w; j += blockDim.x) W.w[j] = 0;
+      st = correct(v, kv, W.r, W.w, nw + 1 < W.cap_w ? nw + 1 : W.cap_w, scr);
+      __syncthreads();
+      const int pw = blk_prec(W.w, W.cap_w, scr);
+      if (pw > nq && st == BIGINT_OK) st = BIGINT_ERANGE;
+      for (int j = threadIdx.x; j < nq; j += blockDim.x) q[j] = j < W.cap_w ? W.w[j] : 0;
+      return;
+    }
+
+    // ---- division
+    st = divmod_one<RB, Q, F, TC>(U + inst * (int64_t)nu, nu, v, nv, q, nq,
+                                  Ro + inst * (int64_t)nv, ws + inst * ws_stride, smem,
+                                  smem_words, scr, tc);
+  }();
+
+  if constexpr (TC) {
+    if (tcc.aborted) st = BIGINT_ETIMEOUT;
+    tcm::tc_release<256>(tcc);
+  }
   if (status && threadIdx.x == 0) status[inst] = st;
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Division kernels for H >= DIV_SMALL_LIMBS run their large products on the
+// tensor cores unless switched off (bigint_set_variant(1, ...)).
+static int g_div_tc = 1;
+
+int div_set_variant(int v) {
+  if (v < 0 || v > 2) return BIGINT_EINVAL;
+  g_div_tc = v != 2;
+  return BIGINT_OK;
+}
+
+// BIGINT_ETIMEOUT if a division kernel's tensor-core product hit a wait
+// limit since the last call (synchronises the device), else BIGINT_OK.
+int div_take_timeout() {
+  BIGINT_CUDA_TRY(cudaDeviceSynchronize());
+  int v = 0;
+  BIGINT_CUDA_TRY(cudaMemcpyFromSymbol(&v, tcm::g_timeout, sizeof(int)));
+  if (v) {
+    const int zero = 0;
+    BIGINT_CUDA_TRY(cudaMemcpyToSymbol(tcm::g_timeout, &zero, sizeof(int)));
+    return BIGINT_ETIMEOUT;
+  }
+  return BIGINT_OK;
+}
+
 static int div_smem_optin() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -111,7 +154,7 @@ size_t shinv_workspace(int64_t count, int nv, int h) {
   return (size_t)count * (size_t)ws_limbs(nv, nv, h) * sizeof(uint64_t);
 }
 
-template <int RB, int Q, int F>
+template <int RB, int Q, int F, bool TC>
 static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                               int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
                               int h, void *ws, cudaStream_t st) {
@@ -120,27 +163,40 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
   static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
   if (dyn_max < 0) {
     cudaFuncAttributes fa;
-    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_divmod<RB, Q, F>));
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_divmod<RB, Q, F, TC>));
     dyn_max = optin - (int)fa.sharedSizeBytes;
-    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_divmod<RB, Q, F>,
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_divmod<RB, Q, F, TC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   }
   int smem_words = dyn_max / 4;
   // the largest product a division performs is about (2 H) x H limbs;
   // ask for no more shared memory than one such product needs
   const int H = (mode == 0 ? nu : h);
-  const int need = blk_mul_smem_words<RB, Q>(H, H);
+  int need = blk_mul_smem_words<RB, Q>(H, H);
+  if (TC) {  // tensor-core products: shorter operand up to max(H - nv, nv) + a few limbs
+    const int ns = (H - nv > nv ? H - nv : nv) + 8;
+    const tcm::Layout L8 = tcm::layout<256, 8>(ns, H + 8);
+    const tcm::Layout L4 = tcm::layout<256, 4>(ns, H + 8);
+    const int w8 = (int)(L8.total / 4), w4 = (int)(L4.total / 4);
+    const int tcw = w8 <= smem_words ? w8 : w4;
+    if (tcw > need) need = tcw;
+  }
   if (need < smem_words) smem_words = need;
-  const int units = blk_mul_units<RB, Q>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
-  constexpr int TMAX = div_max_threads<Q>();
-  int T = (units + TMAX - 1) / TMAX;
-  T = (units + T - 1) / T;
-  T = (T + 31) / 32 * 32;
-  if (T < 64) T = 64;
-  if (T > TMAX) T = TMAX;
+  int T;
+  if (TC) {
+    T = 512;
+  } else {
+    const int units = blk_mul_units<RB, Q>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
+    constexpr int TMAX = div_max_threads<Q, TC>();
+    T = (units + TMAX - 1) / TMAX;
+    T = (units + T - 1) / T;
+    T = (T + 31) / 32 * 32;
+    if (T < 64) T = 64;
+    if (T > TMAX) T = TMAX;
+  }
   const int hcap = mode == 0 ? nu : h;
   const int64_t stride = ws_limbs(nu, nv, hcap);
-  k_divmod<RB, Q, F><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
+  k_divmod<RB, Q, F, TC><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
       u, v, q, r, status, nu, nv, nq, mode, h, reinterpret_cast<uint64_t *>(ws), stride,
       smem_words);
   return bigint_launch_status();
@@ -151,8 +207,13 @@ static int launch_div_common(const uint64_t *u, const uint64_t *v, uint64_t *q, 
                              int h, void *ws, cudaStream_t st) {
   const int H = (mode == 0 ? nu : h);
   if (H < DIV_SMALL_LIMBS)
-    return launch_div_variant<SRB, SQ, SF>(u, v, q, r, status, count, nu, nv, nq, mode, h, ws, st);
-  return launch_div_variant<DRB, DQ, DF>(u, v, q, r, status, count, nu, nv, nq, mode, h, ws, st);
+    return launch_div_variant<SRB, SQ, SF, false>(u, v, q, r, status, count, nu, nv, nq, mode, h,
+                                                  ws, st);
+  if (g_div_tc)
+    return launch_div_variant<DRB, DQ, DF, true>(u, v, q, r, status, count, nu, nv, nq, mode, h,
+                                                 ws, st);
+  return launch_div_variant<DRB, DQ, DF, false>(u, v, q, r, status, count, nu, nv, nq, mode, h,
+                                                ws, st);
 }
 
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,

@@ -1,490 +1,28 @@
-// tcmul.cu -- exact full products on the 5th-generation tensor cores.
+// tcmul.cu -- batched full (and low-part) products on the tensor cores.
 //
-// The schoolbook product of Sec. V-B is a convolution of digit sequences:
-// coefficient s of x*y is sum_i x_i y_(s-i).  This kernel evaluates that
-// convolution as fp16 matrix products with fp32 accumulators (tcgen05.mma,
-// accumulators in tensor memory), exactly:
-//
-//  * Digits.  Each operand is read as base-256 digits (its bytes) recoded to
-//    signed digits e_i = sext(d_i) + top_bit(d_(i-1)) in [-128, 128], plus one
-//    extra digit e_(8n) = top_bit(d_(8n-1)) in {0, 1}; sum e_i 256^i is the
-//    operand again.  Every digit is an exact fp16 value and every digit
-//    product is at most 2^14 in magnitude.
-//  * Blocks.  Output coefficients are grouped in columns of 128 (column c
-//    holds s = 128 c + t).  With x cut into blocks of 128 digits,
-//      coef(128 c + t) = sum_e sum_i A_e[t][i] * x[128 (c - e) + i],
-//      A_e[t][i] = y[128 e + t - i]            (a Toeplitz block of y),
-//    i.e. for each e one MMA with M = 128 (t), K = 128 (i), N = columns c,
-//    whose B operand is x shifted by e blocks.  Summing over e is the K loop.
-//  * Layouts (no swizzle, K-major core matrices of 8 rows x 16 bytes).
-//    B: x is stored once per instance as 16-byte chunks "8 digits of block
-//    p", chunk (p, h) at (p + 16 + h P) * 16 bytes; 8 consecutive blocks are
-//    then 128 bytes apart (stride offset 128) and the 16 digit groups of a
-//    block P*16 bytes apart (leading offset), so shifting by e blocks is a
-//    shift of the descriptor's start address by 16 e bytes.  A: storing the
-//    rows in reverse (TMEM lane t' holds t = 127 - t'), A_e[t'][i] depends
-//    on t' + i only, so its 8x8 core matrix (g, h) depends on g + h only:
-//    core matrix j = "8 rows of 8 digits, row r starting at digit 8j + r" of
-//    the reversed digit stream, and a descriptor with leading and stride
-//    offsets both 128 bytes reads the whole 128 x 128 Toeplitz block from
-//    31 such 128-byte core matrices (a group of G blocks needs 16 G + 15).
-//  * Exactness.  Each accumulator sums at most G x 128 products between
-//    drains: every partial sum is an integer of magnitude at most
-//    G * 2^21 <= 2^24 (G = 8), and all integers up to 2^24 are exact in fp32
-//    and in the tensor core's fp32 accumulation (the byte pattern 0x7F80...
-//    makes every digit +-128 and every product of a column the same sign,
-//    reaching 2^24 exactly; it is a parity case).  The accumulator is then
-//    converted exactly (cvt.rni) and added to int32 column sums in
-//    registers; a column sum is at most (8 n + 1) * 2^14 < 2^31 for
-//    n <= 16383 limbs.
-//  * Output.  Each limb j is V_j = sum_k (coef(8j+k) + 2^31) 2^(8k) (biased
-//    so that all terms are unsigned): the limb's low 64 bits plus a high word
-//    that goes to limb j + 1 in one carry scan per tile (blk_addsub, the
-//    carry scan of Fig. 3), and the bias sum 2^31 sum_s 2^(8s) -- the word
-//    0x8080808080808080 in every limb, 0x8080808080000000 in limb 0 -- is
-//    subtracted at the end with one more borrow scan.
-//
-// Schedule: a persistent CTA of 2 NT threads loops over instances; per
-// instance over tiles of NT output columns; per tile over groups of G = 8
-// Toeplitz blocks (G = 4 when the longer Hankel buffers do not fit).  Fewer,
-// larger groups matter: every drain reads the whole accumulator out of
-// tensor memory, and the drains do not fully overlap the MMAs.  Thread 0 issues a group's MMAs into one of two NT-column
-// fp32 accumulators in tensor memory and commits them to an mbarrier; while
-// they run, all threads build the next group's Hankel core matrices (double
-// buffered) and drain the other accumulator.  NT = 256 (one CTA per SM, all
-// of its tensor memory) serves large products; NT = 128 (two CTAs per SM,
-// half the tensor memory each) keeps more work in flight for small ones.
-// Every wait has a cycle limit;
-// a CTA that reaches it stops, records the event for bigint_check_timeout()
-// and releases its tensor memory.
-#include <cuda_fp16.h>
-
-#include "blockops.cuh"
+// One persistent CTA per SM (NT = 256) or two (NT = 128) loops over the
+// instances of a uniform batch, each product computed by tc_product
+// (tccore.cuh: the digit convolution as tcgen05 fp16 MMAs with exact fp32
+// accumulation, Sec. V-B's schoolbook product on the tensor cores).
+#include "tccore.cuh"
 
 namespace bigint {
 namespace tcm {
-
-// G: Toeplitz blocks per accumulation group; a group's Hankel buffer holds
-// 16 G + 15 core matrices.
-__host__ __device__ constexpr int hankel_blocks(int G) { return 16 * G + 15; }
-constexpr int ZB = 18;           // zero core matrices (operand of the clearing MMA)
-// NT: output columns per tile (= MMA N at most); 2 NT threads, 2 NT TMEM
-// columns (two accumulators).
-constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles, about one second
-// kind::f16 instruction descriptor: fp32 accumulator (bits 4-5 = 1), fp16 A
-// and B (bits 7-12 = 0), both K-major (bits 15, 16 = 0), M = 128 (bits
-// 24-28 = M >> 4); N >> 3 goes to bits 17-22.
-constexpr uint32_t IDESC_M128 = (1u << 4) | ((uint32_t)(128 >> 4) << 24);
-
-__device__ int g_timeout = 0;
-
-struct Layout {
-  int mx;    // x blocks of 128 digits (8 nx + 1 digits)
-  int ey;    // last Toeplitz block index of y (e in [0, ey])
-  int ctot;  // output columns with nonzero coefficients: mx + ey
-  int ptot;  // stored x blocks (16 zero blocks on each side)
-  uint32_t xs, z, h0, h1, cs, his, total;  // byte offsets in dynamic shared memory
-};
-
-template <int NT, int G>
-__host__ __device__ inline Layout layout(int nx, int ny) {
-  constexpr int HB = hankel_blocks(G);
-  Layout L;
-  L.mx = (8 * nx + 1 + 127) / 128;
-  L.ey = (8 * ny + 127) / 128;
-  L.ctot = L.mx + L.ey;
-  L.ptot = L.mx + 32;
-  L.xs = 0;
-  L.z = (uint32_t)L.ptot * 256u;
-  L.h0 = L.z + ZB * 128;
-  L.h1 = L.h0 + HB * 128;
-  L.cs = L.h1 + HB * 128;
-  L.his = L.cs + 32 * 128 * 4;
-  L.total = L.his + NT * 16 * 4;
-  return L;
-}
-
-// ---- PTX wrappers ----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared memory matrix descriptor, no swizzle: start address, leading
-// (K-direction) and stride (M/N-direction) byte offsets, all >> 4, and the
-// fixed version bits 46-48 = 0b001.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Waits for the phase with this parity to complete; false after WAIT_LIMIT
-// cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(mbar, parity))
-    if (clock64() - t0 > WAIT_LIMIT) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Orders this thread's shared memory stores before later tensor-core reads.
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// 32 TMEM lanes (one per thread of the warp) x 16 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// ---- digits ----------------------------------------------------------------
-// Recoded digits e[k] at positions lo + k (k = 0..7) of the n-limb number v:
-// e = sext(byte(pos)) + top_bit(byte(pos - 1)); bytes outside [0, 8n) are 0,
-// so position 8n carries the top bit of the last byte and later ones are 0.
-__device__ __forceinline__ void digits8(const uint64_t *v, int n, int64_t lo, int (&e)[8]) {
-  const int64_t p = lo - 1;
-  const int64_t la = p >> 3;  // floor
-  const int sh = (int)(p & 7) * 8;
-  const uint64_t A = (la >= 0 && la < n) ? __ldg(v + la) : 0ull;
-  const uint64_t B = (la + 1 >= 0 && la + 1 < n) ? __ldg(v + la + 1) : 0ull;
-  const uint64_t w = sh ? (A >> sh) | (B << (64 - sh)) : A;  // bytes p .. p+7
-  const uint32_t b8 = (uint32_t)(B >> sh) & 0xFFu;           // byte p+8
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const uint32_t d = k < 7 ? (uint32_t)(w >> (8 * (k + 1))) & 0xFFu : b8;
-    const int c = (int)((w >> (8 * k + 7)) & 1u);
-    e[k] = (int)(int8_t)(uint8_t)d + c;
-  }
-}
-
-// Two small integers (|v| <= 512) as an fp16 pair: 1536 + v has ulp 1 in
-// fp16, so its bit pattern is 0x6600 + v, and subtracting 1536 is exact.
-__device__ __forceinline__ uint32_t pack_h2(int lo, int hi) {
-  const uint32_t m = 0x66006600u + (uint32_t)lo + ((uint32_t)hi << 16);
-  const __half2 a = __halves2half2(__ushort_as_half((unsigned short)(m & 0xFFFFu)),
-                                   __ushort_as_half((unsigned short)(m >> 16)));
-  const __half2 r = __hsub2(a, __half2half2(__ushort_as_half((unsigned short)0x6600u)));
-  return (uint32_t)__half_as_ushort(__low2half(r)) |
-         ((uint32_t)__half_as_ushort(__high2half(r)) << 16);
-}
-
-// x blocks p in [-16, mx + 16) into the B layout (chunk (p, h) = digits
-// 128 p + 8 h .. + 8, stored at ((p + 16) + h ptot) * 16).
-__device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, int ptot) {
-  for (int idx = threadIdx.x; idx < 16 * ptot; idx += blockDim.x) {
-    const int h = idx / ptot, pp = idx - h * ptot;
-    const int64_t L = 16ll * (pp - 16) + h;
-    int e[8];
-    digits8(x, nx, 8 * L, e);
-    uint4 v;
-    v.x = pack_h2(e[0], e[1]);
-    v.y = pack_h2(e[2], e[3]);
-    v.z = pack_h2(e[4], e[5]);
-    v.w = pack_h2(e[6], e[7]);
-    *reinterpret_cast<uint4 *>(xs + (size_t)idx * 16) = v;
-  }
-}
-
-// Hankel core matrices of the group whose last block is eb: matrix j, row r,
-// element w = recoded y digit at 128 eb + 127 - 8 j - r - w.
-template <int G>
-__device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, int eb) {
-  constexpr int HB = hankel_blocks(G);
-  const int64_t ytop = 128ll * eb + 127;
-  for (int row = threadIdx.x; row < HB * 8; row += blockDim.x) {
-    const int j = row >> 3, r = row & 7;
-    const int64_t yhi = ytop - 8 * j - r;
-    int e[8];
-    digits8(y, ny, yhi - 7, e);  // e[k] = digit yhi - 7 + k; element w = e[7 - w]
-    uint4 v;
-    v.x = pack_h2(e[7], e[6]);
-    v.y = pack_h2(e[5], e[4]);
-    v.z = pack_h2(e[3], e[2]);
-    v.w = pack_h2(e[1], e[0]);
-    *reinterpret_cast<uint4 *>(hb + row * 16) = v;
-  }
-}
-
-// Thread 0: the MMAs of one group (blocks ea..eb) into the accumulator at
-// TMEM column dtm, then a commit to mbar.  For block e only the columns of
-// the tile that meet x (c - e in [0, mx)) are computed, widened to multiples
-// of 16; the group's first MMA overwrites the accumulator if it spans the
-// whole tile, otherwise a clearing MMA with a zero A operand comes first.
-__device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t xs_a,
-                                            uint32_t z_a, uint32_t lbo_b, int c0, int W, int ea,
-                                            int eb, int mx, uint32_t mbar) {
-  tc_fence_after();
-  bool first = true;
-  for (int e = ea; e <= eb; e++) {
-    const int ca = (c0 > e ? c0 : e) - c0;
-    const int cb = (c0 + W < e + mx ? c0 + W : e + mx) - c0;
-    const int lo = ca & ~15, hi = (cb + 15) & ~15;
-    const uint32_t id = IDESC_M128 | ((uint32_t)((hi - lo) >> 3) << 17);
-    const uint32_t aa = ha + (uint32_t)(16 * (eb - e)) * 128u;
-    const uint32_t ba = xs_a + (uint32_t)(c0 + lo - e + 16) * 16u;
-    uint32_t accf = 1;
-    if (first) {
-      first = false;
-      if (lo == 0 && hi == W) {
-        accf = 0;
-      } else {
-        mma_f16(dtm, sdesc(z_a, 128, 128), sdesc(xs_a, lbo_b, 128),
-                IDESC_M128 | ((uint32_t)(W >> 3) << 17), 0);
-      }
-    }
-    // K steps of 16 digits: A moves by 2 core matrices (256 bytes), B by two
-    // leading offsets; the start-address field is bits 0-13 (address >> 4)
-    uint64_t da = sdesc(aa, 128, 128), db = sdesc(ba, lbo_b, 128);
-    const uint64_t step_b = (2u * lbo_b) >> 4;
-#pragma unroll
-    for (int s = 0; s < 8; s++) {
-      mma_f16(dtm + (uint32_t)lo, da, db, id, s == 0 ? accf : 1u);
-      da += 16;
-      db += step_b;
-    }
-  }
-  mma_commit(mbar);
-}
-
-// Adds the accumulator (this warp's 32 lanes, its 64-column slice) to the
-// thread's int32 column sums; the values are integers below 2^24.
-__device__ __forceinline__ void drain(uint32_t taddr, int cq, int W, int (&acc)[64]) {
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const int col = 64 * cq + 16 * k;
-    if (col < W) {
-      uint32_t r[16];
-      tmem_ld16(taddr + (uint32_t)col, r);
-      tmem_ld_wait();
-#pragma unroll
-      for (int i = 0; i < 16; i++) acc[16 * k + i] += __float2int_rn(__uint_as_float(r[i]));
-    }
-  }
-}
 
 template <int NT, int G>
 __global__ void __launch_bounds__(2 * NT, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
              uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count) {
-  constexpr int THREADS = 2 * NT, TMEM_COLS = 2 * NT;
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ uint32_t tmem_slot;
+  __shared__ TcShared sh;
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
-  __shared__ uint32_t s_carry[2];  // high word of the previous tile's last limb, carry
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Layout Ly = layout<NT, G>(nx, ny);
-  const uint32_t sbase = smem_u32(sm);
-  const uint32_t xs_a = sbase + Ly.xs, z_a = sbase + Ly.z;
-  const uint32_t lbo_b = (uint32_t)Ly.ptot * 16u;
-  uint32_t *Cs = reinterpret_cast<uint32_t *>(sm + Ly.cs);
-  uint32_t *His = reinterpret_cast<uint32_t *>(sm + Ly.his);
-  const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-
-  for (int i = tid; i < ZB * 128 / 16; i += THREADS)
-    reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (tid == 0) {
-    mbar_init(mb[0], 1);
-    mbar_init(mb[1], 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(smem_u32(&tmem_slot), TMEM_COLS);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-
-  const int q = warp & 3, cq = warp >> 2;  // TMEM lane quadrant, 64-column slice
-  const uint32_t t_lane = tmem + ((uint32_t)(32 * q) << 16);
-  uint32_t phase0 = 0, phase1 = 0;  // parity of the next completion per buffer
-  int pending0 = 0, pending1 = 0;   // committed groups not yet waited for
-  bool aborted = false;
-  int acc[64];
-
-  for (int64_t inst = blockIdx.x; inst < count && !aborted; inst += gridDim.x) {
-    const uint64_t *x = X + inst * (int64_t)nx;
-    const uint64_t *y = Y + inst * (int64_t)ny;
-    uint64_t *out = Out + inst * (int64_t)nout;
-    fill_x(sm + Ly.xs, x, nx, Ly.ptot);
-    if (tid == 0) { s_carry[0] = 0; s_carry[1] = 0; }
-    fence_async_smem();
-    __syncthreads();
-
-    for (int c0 = 0; 16 * c0 < nout; c0 += NT) {
-      int W = Ly.ctot - c0;
-      if (W > NT) W = NT;
-      W = (W + 15) & ~15;
-      const int e_lo = c0 - Ly.mx + 1 > 0 ? c0 - Ly.mx + 1 : 0;
-      const int e_hi = c0 + W - 1 < Ly.ey ? c0 + W - 1 : Ly.ey;
-      const int NG = e_hi >= e_lo ? (e_hi - e_lo + G) / G : 0;
-#pragma unroll
-      for (int i = 0; i < 64; i++) acc[i] = 0;
-      if (NG > 0) {
-        build_h<G>(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi);
-        fence_async_smem();
-        __syncthreads();
-        bool bad = false;
-        for (int gi = 0; gi < NG; gi++) {
-          const int b = gi & 1;
-          const int ea = e_lo + gi * G, eb = ea + G - 1 < e_hi ? ea + G - 1 : e_hi;
-          if (tid == 0)
-            issue_group(tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a, z_a,
-                        lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
-          if (b) pending1++; else pending0++;
-          if (gi >= 1) {  // group gi-1 used the other buffers
-            const int ob = b ^ 1;
-            if (!mbar_wait(mb[ob], ob ? phase1 : phase0)) bad = true;
-            if (ob) { phase1 ^= 1; pending1--; } else { phase0 ^= 1; pending0--; }
-            tc_fence_after();
-            drain(t_lane + (uint32_t)(ob * NT), cq, W, acc);
-          }
-          if (gi + 1 < NG) {
-            const int na = ea + G, nb2 = na + G - 1 < e_hi ? na + G - 1 : e_hi;
-            build_h<G>(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2);
-          }
-          tc_fence_before();
-          fence_async_smem();
-          if (__syncthreads_or(bad)) { aborted = true; break; }
-        }
-        if (!aborted) {
-          const int lb = (NG - 1) & 1;
-          if (!mbar_wait(mb[lb], lb ? phase1 : phase0)) bad = true;
-          if (lb) { phase1 ^= 1; pending1--; } else { phase0 ^= 1; pending0--; }
-          tc_fence_after();
-          drain(t_lane + (uint32_t)(lb * NT), cq, W, acc);
-          tc_fence_before();
-          if (__syncthreads_or(bad)) aborted = true;
-        }
-      }
-      if (aborted) break;
-
-      // ---- column sums -> limbs of this tile (low words to out, high words to His)
-      const int j0 = 16 * c0;
-      const int nl = 16 * W < nout - j0 ? 16 * W : nout - j0;
-#pragma unroll
-      for (int rr = 0; rr < NT / 32; rr++) {
-        if (32 * rr < W) {
-          if (cq == (rr >> 1)) {
-            const int t = 127 - (32 * q + lane);
-#pragma unroll
-            for (int i = 0; i < 32; i++) Cs[i * 128 + t] = (uint32_t)acc[(rr & 1) * 32 + i];
-          }
-          __syncthreads();
-          for (int idx = tid; idx < 32 * 16; idx += THREADS) {  // 32 columns x 16 limbs
-            const int col = idx >> 4, jj = idx & 15;
-            const int lt = (32 * rr + col) * 16 + jj;
-            if (lt < nl) {
-              const uint4 u0 = *reinterpret_cast<const uint4 *>(&Cs[col * 128 + 8 * jj]);
-              const uint4 u1 = *reinterpret_cast<const uint4 *>(&Cs[col * 128 + 8 * jj + 4]);
-              const uint32_t cw[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-              unsigned __int128 V = 0;
-#pragma unroll
-              for (int k = 0; k < 8; k++)
-                V += (unsigned __int128)(cw[k] ^ 0x80000000u) << (8 * k);
-              out[j0 + lt] = (uint64_t)V;
-              His[lt] = (uint32_t)(V >> 64);
-            }
-          }
-          __syncthreads();
-        }
-      }
-      {
-        const uint64_t hprev = s_carry[0];
-        const uint32_t cprev = s_carry[1];
-        uint64_t *o = out + j0;
-        auto load = [&](int j) {
-          return make_ulonglong2(o[j], j == 0 ? hprev : (uint64_t)His[j - 1]);
-        };
-        auto store = [&](int j, uint64_t v) { o[j] = v; };
-        const uint32_t cout = blk_addsub<false>(nl, cprev, load, store, scr);
-        if (tid == 0) { s_carry[0] = His[nl - 1]; s_carry[1] = cout; }
-        __syncthreads();
-      }
-    }
-    if (aborted) break;
-    {  // subtract the bias sum 2^31 sum_s 2^(8 s)
-      auto load = [&](int j) {
-        return make_ulonglong2(out[j], j == 0 ? 0x8080808080000000ull : 0x8080808080808080ull);
-      };
-      auto store = [&](int j, uint64_t v) { out[j] = v; };
-      blk_addsub<true>(nout, 0u, load, store, scr);
-    }
-    __syncthreads();
-  }
-
-  if (aborted) {  // wait (bounded) for MMAs still in flight before releasing TMEM
-    if (pending0 > 0) mbar_wait(mb[0], phase0);
-    if (pending1 > 0) mbar_wait(mb[1], phase1);
-    if (tid == 0) atomicExch(&g_timeout, 1);
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+  TcCtx c;
+  tc_init<NT>(c, sm, &sh, scr);
+  for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x)
+    if (!tc_product<NT, G>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
+                           Out + inst * (int64_t)nout, nout, 0))
+      break;
+  tc_release<NT>(c);
 }
 
 }  // namespace tcm
