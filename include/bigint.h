@@ -215,6 +215,37 @@ int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
 int bigint_tuning_save(const char *path);
 int bigint_tuning_load(const char *path);
 
+/* ---- host-buffer entry points --------------------------------------------
+ * The operations above on operands and results in HOST memory.  The library
+ * splits the batch into chunks and overlaps, on three streams of its own,
+ * the host->device copy of chunk i+1, the kernel of chunk i and the
+ * device->host copy of chunk i-1 (two staging slots in `workspace`, device
+ * memory of `bytes` bytes, 256-byte aligned); the call returns when all
+ * results are in host memory (synchronous; not thread-safe).  Host buffers
+ * should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap; pageable buffers give the same results more slowly.  Layouts and
+ * result semantics are those of the device entry points: a, b instance-major
+ * limb arrays, carry/borrow one byte and status one int32 per instance (these
+ * may be NULL: not returned).  Returns BIGINT_EINVAL for bad shapes, null or
+ * misaligned buffers, BIGINT_ENOMEM if two slots of one instance do not fit
+ * `bytes`, BIGINT_ECUDA for a CUDA error.  The paper has no counterpart
+ * (its measurements keep data on the device); this is the library's own
+ * end-to-end path.
+ *
+ * bigint_host_workspace: bytes of workspace for chunks of `chunk` instances
+ * of op (BIGINT_OP_ADD .. BIGINT_OP_DIVMOD; for divmod na = nu, nb = nv);
+ * 0 for invalid arguments. */
+size_t bigint_host_workspace(int op, int64_t chunk, int32_t na, int32_t nb);
+int bigint_add_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
+                    int64_t count, int32_t n, void *workspace, size_t bytes);
+int bigint_sub_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *borrow_out,
+                    int64_t count, int32_t n, void *workspace, size_t bytes);
+int bigint_mul_host(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                    int32_t na, int32_t nb, void *workspace, size_t bytes);
+int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                       int32_t *status, int64_t count, int32_t nu, int32_t nv,
+                       void *workspace, size_t bytes);
+
 /* ---- tuning and measurement ---------------------------------------------
  * Selects the kernel variant an operation uses from now on (process-wide,
  * not thread-safe; call it before launching work).  op 0 = multiply:

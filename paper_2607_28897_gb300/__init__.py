@@ -17,6 +17,7 @@ import os
 __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "divmod_noalloc", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
+    "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host",
     "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
     "MAX_LIMBS", "MUL_MAX_LIMBS",
 ]
@@ -59,6 +60,11 @@ SIGNATURES = {
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
     "bigint_check_timeout": ([], ctypes.c_int),
+    "bigint_host_workspace": ([ctypes.c_int, _I64, _I32, _I32], _SZ),
+    "bigint_add_host": ([_P, _P, _P, _P, _I64, _I32, _P, _SZ], ctypes.c_int),
+    "bigint_sub_host": ([_P, _P, _P, _P, _I64, _I32, _P, _SZ], ctypes.c_int),
+    "bigint_mul_host": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ], ctypes.c_int),
+    "bigint_divmod_host": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ], ctypes.c_int),
     "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -255,6 +261,86 @@ def shinv(v, h: int, nw: int, w=None, status=None, workspace=None, stream=None):
                              _stream_ptr(stream))
     _check(rc, "bigint_shinv")
     return w, status
+
+
+# ---- host-buffer entry points (copies overlapped with the kernels) ----------
+def _host_tensor(x, name: str):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or x.device.type != "cpu" or x.dim() != 2:
+        raise BigIntError(f"{name}: expected a 2-D CPU tensor of limbs (pinned for overlap)")
+    if x.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)) or not x.is_contiguous():
+        raise BigIntError(f"{name}: expected a contiguous int64/uint64 tensor")
+    return x
+
+
+def host_workspace_bytes(op: int, chunk: int, na: int, nb: int) -> int:
+    return int(load().bigint_host_workspace(op, chunk, na, nb))
+
+
+def _host_ws(op, count, na, nb, workspace, device):
+    if workspace is not None:
+        return workspace
+    chunk = max(1, (count + 3) // 4)
+    return _workspace(host_workspace_bytes(op, chunk, na, nb), device)
+
+
+def _host_out(count, n, out):
+    torch = _torch()
+    return torch.empty((count, n), dtype=torch.int64).pin_memory() if out is None else out
+
+
+def add_host(a, b, out=None, carry=None, workspace=None, device="cuda"):
+    """a + b for CPU (pinned) tensors: chunks copied in, added and copied
+    back with the copies overlapping the kernels."""
+    return _addsub_host(load().bigint_add_host, OP_ADD, a, b, out, carry, workspace, device)
+
+
+def sub_host(a, b, out=None, borrow=None, workspace=None, device="cuda"):
+    return _addsub_host(load().bigint_sub_host, OP_SUB, a, b, out, borrow, workspace, device)
+
+
+def _addsub_host(fn, op, a, b, out, flag, workspace, device):
+    torch = _torch()
+    a, b = _host_tensor(a, "a"), _host_tensor(b, "b")
+    count, n = a.shape
+    out = _host_tensor(_host_out(count, n, out), "out")
+    ws = _host_ws(op, count, n, n, workspace, device)
+    rc = fn(a.data_ptr(), b.data_ptr(), out.data_ptr(), flag.data_ptr() if flag is not None else None,
+            count, n, ws.data_ptr(), ws.numel() * ws.element_size())
+    _check(rc, "bigint_add_host" if op == OP_ADD else "bigint_sub_host")
+    return out
+
+
+def mul_host(a, b, out=None, workspace=None, device="cuda"):
+    """Full products of CPU (pinned) tensors, copies overlapped with kernels."""
+    a, b = _host_tensor(a, "a"), _host_tensor(b, "b")
+    count, na = a.shape
+    nb = b.shape[1]
+    out = _host_tensor(_host_out(count, na + nb, out), "out")
+    ws = _host_ws(OP_MUL, count, na, nb, workspace, device)
+    rc = load().bigint_mul_host(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
+                                ws.data_ptr(), ws.numel() * ws.element_size())
+    _check(rc, "bigint_mul_host")
+    return out
+
+
+def divmod_host(u, v, q=None, r=None, status=None, workspace=None, device="cuda"):
+    """q, r (and per-instance status) of CPU (pinned) tensors, copies
+    overlapped with the division kernels."""
+    torch = _torch()
+    u, v = _host_tensor(u, "u"), _host_tensor(v, "v")
+    count, nu = u.shape
+    nv = v.shape[1]
+    q = _host_tensor(_host_out(count, max(nu - nv + 1, 1), q), "q")
+    r = _host_tensor(_host_out(count, nv, r), "r")
+    if status is None:
+        status = torch.empty(count, dtype=torch.int32).pin_memory()
+    ws = _host_ws(OP_DIVMOD, count, nu, nv, workspace, device)
+    rc = load().bigint_divmod_host(u.data_ptr(), v.data_ptr(), q.data_ptr(), r.data_ptr(),
+                                   status.data_ptr(), count, nu, nv, ws.data_ptr(),
+                                   ws.numel() * ws.element_size())
+    _check(rc, "bigint_divmod_host")
+    return q, r, status
 
 
 def set_variant(op: int, variant: int) -> None:

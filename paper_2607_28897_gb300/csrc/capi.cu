@@ -15,6 +15,9 @@ int mul_max_limbs();
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
+size_t host_workspace(int op, int64_t chunk, int na, int nb);
+int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
+             void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes);
 int div_take_timeout();
 int div_set_variant(int v);
 int probe_int_throughput(int variant, double *ops, double *mhz);
@@ -181,6 +184,31 @@ int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);
   if (op == 1) return div_set_variant(variant);
   return BIGINT_EINVAL;
+}
+
+size_t bigint_host_workspace(int op, int64_t chunk, int32_t na, int32_t nb) {
+  return host_workspace(op, chunk, na, nb);
+}
+
+int bigint_add_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
+                    int64_t count, int32_t n, void *workspace, size_t bytes) {
+  return host_run(BIGINT_OP_ADD, a, b, out, nullptr, carry_out, count, n, n, workspace, bytes);
+}
+
+int bigint_sub_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *borrow_out,
+                    int64_t count, int32_t n, void *workspace, size_t bytes) {
+  return host_run(BIGINT_OP_SUB, a, b, out, nullptr, borrow_out, count, n, n, workspace, bytes);
+}
+
+int bigint_mul_host(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                    int32_t na, int32_t nb, void *workspace, size_t bytes) {
+  return host_run(BIGINT_OP_MUL, a, b, out, nullptr, nullptr, count, na, nb, workspace, bytes);
+}
+
+int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                       int32_t *status, int64_t count, int32_t nu, int32_t nv,
+                       void *workspace, size_t bytes) {
+  return host_run(BIGINT_OP_DIVMOD, u, v, q, r, status, count, nu, nv, workspace, bytes);
 }
 
 int bigint_check_timeout(void) {

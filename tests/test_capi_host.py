@@ -71,3 +71,37 @@ def test_tuning_table_rejects_other_gpu(L, tmp_path):
     assert L.bigint_tuning_load(b"/nonexistent/tuning.json") == bi.EINVAL
     assert L.bigint_set_variant(0, 99) == bi.EINVAL
     assert L.bigint_set_variant(7, 0) == bi.EINVAL
+
+
+# ---- host-buffer entry points: argument checks that need no GPU -------------
+def test_host_workspace_rejects_bad_shapes():
+    import paper_2607_28897_gb300 as bi
+
+    lib = bi.load()
+    assert lib.bigint_host_workspace(bi.OP_MUL, 0, 8, 8) == 0
+    assert lib.bigint_host_workspace(bi.OP_ADD, 4, 8, 9) == 0  # add needs na == nb
+    assert lib.bigint_host_workspace(99, 4, 8, 8) == 0
+    assert lib.bigint_host_workspace(bi.OP_MUL, 4, 0, 8) == 0
+    assert lib.bigint_host_workspace(bi.OP_MUL, 4, bi.MUL_MAX_LIMBS + 1, 8) == 0
+    # two staging slots of 4 instances: operands, product, 256-byte aligned
+    assert lib.bigint_host_workspace(bi.OP_MUL, 4, 8, 8) == 2 * (256 + 256 + 512)
+
+
+def test_host_calls_check_arguments():
+    import ctypes
+
+    import paper_2607_28897_gb300 as bi
+
+    lib = bi.load()
+    buf = (ctypes.c_uint64 * 64)()
+    p = ctypes.addressof(buf)
+    # count 0: nothing to do
+    assert lib.bigint_mul_host(None, None, None, 0, 4, 4, None, 0) == bi.OK
+    # null operands, null workspace, misaligned workspace
+    assert lib.bigint_mul_host(None, p, p, 2, 4, 4, p, 1 << 20) == bi.EINVAL
+    assert lib.bigint_mul_host(p, p, p, 2, 4, 4, None, 1 << 20) == bi.EINVAL
+    assert lib.bigint_mul_host(p, p, p, 2, 4, 4, p + 8, 1 << 20) == bi.EINVAL
+    # add/sub need equal lengths; divmod needs the remainder buffer
+    assert lib.bigint_add_host(p, p, p, None, 2, 0, p, 1 << 20) == bi.EINVAL
+    assert lib.bigint_divmod_host(p, p, p, None, None, 2, 4, 2, p, 1 << 20) == bi.EINVAL
+    assert lib.bigint_divmod_host(p, p, p, p, None, -1, 4, 2, p, 1 << 20) == bi.EINVAL
