@@ -273,6 +273,12 @@ int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64
  *   shorter operand has at least 256 limbs on the tensor cores (as variant
  *   12 of the multiply); smaller divisions use the integer products
  *   variant 2: integer products (blk_mul) for every division
+ * op 2 = ragged batches (bigint_batch_*, for batches created afterwards):
+ *   variant 0 (default) or 1: a batch with multiplications or divisions
+ *   whose products have a shorter operand of 256 limbs or more runs them in
+ *   512-thread launches that hold their SM's tensor memory and compute those
+ *   products on the tensor cores (the CTA size tuner then has no choice)
+ *   variant 2: integer products only
  * Returns BIGINT_EINVAL for an unknown op or variant.                      */
 int bigint_set_variant(int op, int variant);
 

@@ -36,9 +36,10 @@ static_assert(sizeof(OpDev) == sizeof(bigint_op), "descriptor layout");
 constexpr int BRB = 29, BQ = 16, BF = 32;
 constexpr int BATCH_MAX_THREADS = 512;
 
+template <bool TC>
 __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uint64_t *out,
                                          uint64_t *ws, uint32_t *smem, int smem_words,
-                                         uint32_t *scr) {
+                                         uint32_t *scr, tcm::TcCtx *tc) {
   switch (o.op) {
     case BIGINT_OP_ADD:
     case BIGINT_OP_SUB: {
@@ -50,26 +51,41 @@ __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uin
                                    : (int)blk_addsub<true>(o.na, 0u, load, store, scr);
     }
     case BIGINT_OP_MUL:
+      if constexpr (TC) {
+        if (tc_mul(tc, in + o.a, o.na, in + o.b, o.nb, out + o.o1, o.na + o.nb, smem_words, 0))
+          return 0;
+      }
       blk_mul_call<BRB, BQ, BF>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, o.na + o.nb, smem, 0);
       return 0;
     case BIGINT_OP_DIVMOD: {
       const int nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
-      return divmod_one<DRB, DQ, DF>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, nq, out + o.o2, ws, smem,
-                        smem_words, scr);
+      return divmod_one<DRB, DQ, DF, TC>(in + o.a, o.na, in + o.b, o.nb, out + o.o1, nq,
+                                         out + o.o2, ws, smem, smem_words, scr, tc);
     }
     default:
       return BIGINT_EINVAL;
   }
 }
 
+// TC: 512 threads holding the SM's tensor memory; products with a shorter
+// operand of TC_DIV_MIN limbs or more (multiplications, and the products
+// inside divisions) run on the tensor cores.
+template <bool TC>
 __global__ void __launch_bounds__(BATCH_MAX_THREADS)
     k_batch(const OpDev *__restrict__ ops, const int32_t *__restrict__ order, int first,
             int count, const uint64_t *in, uint64_t *out, int32_t *status, uint64_t *ws,
             int64_t ws_per_cta, int *queue, int smem_words) {
-  extern __shared__ __align__(16) uint32_t smem[];
+  extern __shared__ __align__(1024) uint32_t smem[];
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   __shared__ int s_idx;
+  __shared__ tcm::TcShared tsh;
   uint64_t *my_ws = ws + (int64_t)blockIdx.x * ws_per_cta;
+  tcm::TcCtx tcc;
+  tcm::TcCtx *tc = nullptr;
+  if constexpr (TC) {
+    tcm::tc_init<256>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
+    tc = &tcc;
+  }
   int stride_idx = blockIdx.x;
   for (;;) {
     int idx;
@@ -85,10 +101,14 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS)
     if (idx >= count) break;
     const int opi = order[first + idx];
     const OpDev o = ops[opi];
-    const int st = op_status(o, in, out, my_ws, smem, smem_words, scr);
+    int st = op_status<TC>(o, in, out, my_ws, smem, smem_words, scr, tc);
+    if constexpr (TC) {
+      if (tcc.aborted) st = BIGINT_ETIMEOUT;
+    }
     if (status != nullptr && threadIdx.x == 0) status[opi] = st;
     __syncthreads();
   }
+  if constexpr (TC) tcm::tc_release<256>(tcc);
 }
 
 // ---------------------------------------------------------------------------
@@ -122,6 +142,30 @@ int op_smem_words(const bigint_op &o) {
   return BLK_SCRATCH_WORDS;
 }
 
+// Operations that use the tensor cores in a TC launch, and the shared
+// memory (words) their largest tensor-core product needs.
+bool op_tc(const bigint_op &o) {
+  if (o.op == BIGINT_OP_MUL) return std::min(o.na, o.nb) >= TC_DIV_MIN;
+  if (o.op == BIGINT_OP_DIVMOD) return o.nb >= TC_DIV_MIN || o.na - o.nb >= TC_DIV_MIN;
+  return false;
+}
+
+int op_tc_words(const bigint_op &o, int max_words) {
+  int ns, nl;
+  if (o.op == BIGINT_OP_MUL) {
+    ns = std::min(o.na, o.nb);
+    nl = std::max(o.na, o.nb);
+  } else if (o.op == BIGINT_OP_DIVMOD) {
+    ns = std::max(o.na - o.nb, o.nb) + 8;
+    nl = o.na + 8;
+  } else {
+    return 0;
+  }
+  const int w8 = (int)(tcm::layout<256, 8>(ns, nl).total / 4);
+  const int w4 = (int)(tcm::layout<256, 4>(ns, nl).total / 4);
+  return w8 <= max_words ? w8 : w4;
+}
+
 int op_units(const bigint_op &o) {
   const int a = std::min(o.na, 8192), b = std::min(o.nb, 8192);
   if (o.op == BIGINT_OP_MUL) return blk_mul_units<BRB, BQ>(a, b);
@@ -140,9 +184,18 @@ int g_batch_threads = 0;  // tuned CTA size of persistent launches (0: from the 
 
 struct Launch {
   int first, count, threads, ctas, smem_words;
+  bool tc;  // k_batch<true>: 512 threads, one CTA per SM, tensor-core products
 };
 
 }  // namespace
+
+int g_batch_tc = 1;  // tensor-core launches for new batches (bigint_set_variant(2, ...))
+
+int batch_set_variant(int v) {
+  if (v < 0 || v > 2) return BIGINT_EINVAL;
+  g_batch_tc = v != 2;
+  return BIGINT_OK;
+}
 
 int batch_set_threads(int t) {
   if (t != 0 && (t < 64 || t > BATCH_MAX_THREADS || t % 32)) return BIGINT_EINVAL;
@@ -166,24 +219,38 @@ struct bigint_batch {
   size_t workspace_bytes = 0;
   int sms = 0, optin = 0;
   int threads_override = 0;  // set by the tuner for this batch
+  bool use_tc = true;        // tensor-core launches for large products (batch_set_tc)
 };
 
 namespace bigint {
 namespace {
 
-constexpr int STATIC_SMEM = BLK_SCRATCH_WORDS * 4 + 16;
-
-int occupancy(int threads, int smem_words, int *per_sm) {
-  static bool configured = false;
-  int dev = 0, optin = 0;
-  BIGINT_CUDA_TRY(cudaGetDevice(&dev));
-  BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (!configured) {
-    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         optin - STATIC_SMEM));
-    configured = true;
+// Largest dynamic shared memory (words) of a k_batch<TC> launch.
+template <bool TC>
+int max_dyn_words() {
+  static int words = -1;
+  if (words < 0) {
+    int dev = 0, optin = 0;
+    BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+    BIGINT_CUDA_TRY(
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_batch<TC>));
+    const int bytes = optin - (int)fa.sharedSizeBytes;
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_batch<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         bytes));
+    words = bytes / 4;
   }
-  BIGINT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch, threads,
+  return words;
+}
+
+int occupancy(bool tc, int threads, int smem_words, int *per_sm) {
+  if (tc) {  // all 512 TMEM columns: one CTA per SM
+    *per_sm = 1;
+    return max_dyn_words<true>() < 0 ? BIGINT_ECUDA : BIGINT_OK;
+  }
+  if (max_dyn_words<false>() < 0) return BIGINT_ECUDA;
+  BIGINT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<false>, threads,
                                                                 (size_t)smem_words * 4));
   if (*per_sm < 1) *per_sm = 1;
   return BIGINT_OK;
@@ -195,21 +262,34 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 int batch_configure(bigint_batch *B) {
   const int64_t n = (int64_t)B->ops.size();
-  const int max_words = (B->optin - STATIC_SMEM) / 4;
+  const int max_words = max_dyn_words<false>(), max_words_tc = max_dyn_words<true>();
+  if (max_words < 0 || max_words_tc < 0) return BIGINT_ECUDA;
   // persistent launch: one shape for every operation
-  int words = BLK_SCRATCH_WORDS, units = 32;
+  int words = BLK_SCRATCH_WORDS, units = 32, tc_words = 0;
+  bool tc = false;
   for (const bigint_op &o : B->ops) {
     words = std::max(words, op_smem_words(o));
     units = std::max(units, op_units(o));
+    if (B->use_tc && op_tc(o)) {
+      tc = true;
+      tc_words = std::max(tc_words, op_tc_words(o, max_words_tc));
+    }
   }
   Launch &P = B->persistent;
   P.first = 0;
   P.count = (int)n;
-  P.smem_words = std::min(words, max_words);
-  P.threads = B->threads_override ? B->threads_override
-                                   : (g_batch_threads ? g_batch_threads : threads_for_units(units));
+  P.tc = tc;
+  if (tc) {
+    P.smem_words = std::min(std::max(words, tc_words), max_words_tc);
+    P.threads = BATCH_MAX_THREADS;
+  } else {
+    P.smem_words = std::min(words, max_words);
+    P.threads = B->threads_override
+                    ? B->threads_override
+                    : (g_batch_threads ? g_batch_threads : threads_for_units(units));
+  }
   int per_sm = 1;
-  int rc = occupancy(P.threads, P.smem_words, &per_sm);
+  int rc = occupancy(P.tc, P.threads, P.smem_words, &per_sm);
   if (rc != BIGINT_OK) return rc;
   P.ctas = B->sms * per_sm;
   B->max_ctas = P.ctas;
@@ -218,20 +298,26 @@ int batch_configure(bigint_batch *B) {
   for (size_t i = 0; i < B->order_classes.size();) {
     const bigint_op &o0 = B->ops[B->order_classes[i]];
     size_t j = i;
-    int w = BLK_SCRATCH_WORDS, u = 32;
+    int w = BLK_SCRATCH_WORDS, u = 32, tw = 0;
+    bool ltc = false;
     while (j < B->order_classes.size()) {
       const bigint_op &o = B->ops[B->order_classes[j]];
       if (o.op != o0.op || size_class(o) != size_class(o0)) break;
       w = std::max(w, op_smem_words(o));
       u = std::max(u, op_units(o));
+      if (B->use_tc && op_tc(o)) {
+        ltc = true;
+        tw = std::max(tw, op_tc_words(o, max_words_tc));
+      }
       j++;
     }
     Launch L;
     L.first = (int)i;
     L.count = (int)(j - i);
-    L.smem_words = std::min(w, max_words);
-    L.threads = threads_for_units(u);
-    rc = occupancy(L.threads, L.smem_words, &per_sm);
+    L.tc = ltc;
+    L.smem_words = ltc ? std::min(std::max(w, tw), max_words_tc) : std::min(w, max_words);
+    L.threads = ltc ? BATCH_MAX_THREADS : threads_for_units(u);
+    rc = occupancy(L.tc, L.threads, L.smem_words, &per_sm);
     if (rc != BIGINT_OK) return rc;
     L.ctas = std::min(L.count, B->sms * per_sm);
     B->max_ctas = std::max(B->max_ctas, L.ctas);
@@ -262,6 +348,7 @@ int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out) {
   }
   bigint_batch *B = new bigint_batch;
   B->ops.assign(ops, ops + nops);
+  B->use_tc = g_batch_tc != 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -316,14 +403,16 @@ int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32
     const Launch &P = B->persistent;
     int *queue = reinterpret_cast<int *>(w + B->queue_off);
     BIGINT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
-    k_batch<<<P.ctas, P.threads, (size_t)P.smem_words * 4, st>>>(
+    auto *kern = P.tc ? k_batch<true> : k_batch<false>;
+    kern<<<P.ctas, P.threads, (size_t)P.smem_words * 4, st>>>(
         ops, reinterpret_cast<const int32_t *>(w + B->order_p_off), 0, P.count, in, out, status,
         scratch, B->ws_limbs_per_cta, queue, P.smem_words);
     return bigint_launch_status();
   }
   if (mode != BIGINT_BATCH_PER_CLASS) return BIGINT_EINVAL;
   for (const Launch &L : B->classes) {
-    k_batch<<<L.ctas, L.threads, (size_t)L.smem_words * 4, st>>>(
+    auto *kern = L.tc ? k_batch<true> : k_batch<false>;
+    kern<<<L.ctas, L.threads, (size_t)L.smem_words * 4, st>>>(
         ops, reinterpret_cast<const int32_t *>(w + B->order_c_off), L.first, L.count, in, out,
         status, scratch, B->ws_limbs_per_cta, nullptr, L.smem_words);
     const int rc = bigint_launch_status();

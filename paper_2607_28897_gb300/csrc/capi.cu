@@ -20,6 +20,7 @@ int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, u
              void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes);
 int div_take_timeout();
 int div_set_variant(int v);
+int batch_set_variant(int v);
 int probe_int_throughput(int variant, double *ops, double *mhz);
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                   int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
@@ -183,6 +184,7 @@ int bigint_tuning_load(const char *path) { return path ? tuning_load(path) : BIG
 int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);
   if (op == 1) return div_set_variant(variant);
+  if (op == 2) return batch_set_variant(variant);
   return BIGINT_EINVAL;
 }
 

@@ -123,3 +123,35 @@ def test_batch_tune_and_graph(orc):
     torch.cuda.synchronize()
     check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
     bi.set_variant(0, 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_tensor_cores_equal_integer(orc, mode):
+    """Large ragged operations (up to 6000 limbs): the tensor-core launches
+    (batch variant 0) and integer-only launches (variant 2) give the same
+    bits, and the oracle's."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    ops, nin, nout = inputs.ragged_ops(31, 60, min_limbs=200, max_limbs=6000)
+    pool = inputs.ragged_pool(32, ops, nin)
+    exp, exp_st = oracle_results(orc, ops, pool)
+    dpool = to_dev(pool).view(-1)
+    results = []
+    for variant in (0, 2):
+        bi.set_variant(2, variant)
+        try:
+            dout = torch.zeros(nout, dtype=torch.int64, device="cuda")
+            st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+            bi.Batch(ops).launch(dpool, dout, st, mode=mode)
+            torch.cuda.synchronize()
+            results.append((to_host(dout), st.cpu().numpy()))
+        finally:
+            bi.set_variant(2, 0)
+    bi.check_timeout()
+    (p0, s0), (p2, s2) = results
+    check(ops, p0, s0, exp, exp_st)
+    assert np.array_equal(s0, s2)
+    check(ops, p2, s2, exp, exp_st)
