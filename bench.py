@@ -557,6 +557,24 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
             hu, hv, hq, hr, hst, wsd = hdiv[n]
             bi.divmod_host(hu, hv, q=hq, r=hr, status=hst, workspace=wsd)
 
+    # the host link's copy rate on this machine (differs between machines),
+    # measured outside the timed region on 512 MiB pinned buffers
+    probe_h = torch.empty(1 << 26, dtype=torch.int64).pin_memory()
+    probe_d = torch.empty(1 << 26, dtype=torch.int64, device=dev)
+
+    def copy_gbs(fn):
+        fn()
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        return 3 * probe_h.numel() * 8 / (time.perf_counter() - c0) / 1e9
+
+    h2d_gbs = copy_gbs(lambda: probe_d.copy_(probe_h, non_blocking=True))
+    d2h_gbs = copy_gbs(lambda: probe_h.copy_(probe_d, non_blocking=True))
+    del probe_h, probe_d
+
     step()
     torch.cuda.synchronize()
     if dist:
@@ -570,7 +588,8 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     dt = ranks.max_over_ranks(time.perf_counter() - t0, dist, dev)
     return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "path": "bigint_*_host (C ABI, pinned host buffers, copies overlapped with kernels)"}
+            "path": "bigint_*_host (C ABI, pinned host buffers, copies overlapped with kernels)",
+            "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
 
 def run_batched(args):
     """The batched form: ragged instances (sizes log-uniform over 2^15..2^19

@@ -215,6 +215,28 @@ int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
 int bigint_tuning_save(const char *path);
 int bigint_tuning_load(const char *path);
 
+/* ---- fused programs (Sec. VI, Tables I and II) ----------------------------
+ * bigint_add_chain: out = a + b + ... + b with k additions (1 <= k <= 255),
+ * each a full carry-propagating addition mod B^n (Table I's 6-Add is k = 6);
+ * carry_out[i] = floor((a + k b) / B^n) (may be NULL).  One launch, the
+ * running sum held in registers: global traffic is that of one addition.
+ * a, b, out: count x n limbs, device pointers, out may alias a.
+ *
+ * bigint_poly: out = (a a + b)(b b + b) + a b mod B^n (Table II's Poly: four
+ * multiplications, three additions, every value kept to n limbs as the
+ * paper's same-width multiply and add).  One persistent launch; products of
+ * n >= 256 limbs run on the tensor cores; intermediates live in `workspace`
+ * (device memory of bigint_poly_workspace(count, n) bytes: 3 n limbs per
+ * resident CTA, small enough to stay in L2).  a, b, out: count x n limbs,
+ * out disjoint from a and b.  n <= BIGINT_MUL_MAX_LIMBS.
+ * Both return BIGINT_EINVAL for bad shapes or pointers, BIGINT_ENOMEM for a
+ * short workspace, BIGINT_ECUDA for a launch error.                         */
+int bigint_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
+                     int64_t count, int32_t n, int32_t k, void *stream);
+size_t bigint_poly_workspace(int64_t count, int32_t n);
+int bigint_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int32_t n,
+                void *workspace, size_t bytes, void *stream);
+
 /* ---- host-buffer entry points --------------------------------------------
  * The operations above on operands and results in HOST memory.  The library
  * splits the batch into chunks and overlaps, on three streams of its own,

@@ -67,6 +67,10 @@ def lib():
         L.orc_batch_mul.argtypes = [p, p, p, i64, i64, i64]
         L.orc_batch_divmod.argtypes = [p, p, p, p, p, i64, i64, i64]
         L.orc_num_threads.argtypes = []
+        L.orc_add_chain.argtypes = [p, p, p, i64, i32]
+        L.orc_add_chain.restype = i32
+        L.orc_poly.argtypes = [p, p, p, i64]
+        L.orc_poly.restype = None
         for f in ("orc_add", "orc_sub", "orc_divmod", "orc_shinv", "orc_step",
                   "orc_batch_add", "orc_batch_sub", "orc_batch_mul",
                   "orc_batch_divmod", "orc_num_threads"):
@@ -137,6 +141,20 @@ def step(h: int, m: int, v, w, nout: int):
     out = np.zeros(nout, dtype=np.uint64)
     s = lib().orc_step(h, m, _ptr(v), v.size, _ptr(w), w.size, _ptr(out), nout)
     return out, s
+
+
+def add_chain(a, b, k: int):
+    a, b = _u64(a), _u64(b)
+    out = np.zeros_like(a)
+    c = lib().orc_add_chain(_ptr(a), _ptr(b), _ptr(out), a.size, k)
+    return out, c
+
+
+def poly(a, b):
+    a, b = _u64(a), _u64(b)
+    out = np.zeros_like(a)
+    lib().orc_poly(_ptr(a), _ptr(b), _ptr(out), a.size)
+    return out
 
 
 def prec(x) -> int:

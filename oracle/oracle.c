@@ -439,6 +439,31 @@ int64_t orc_prec(const uint64_t *x, int64_t n)
     return p;
 }
 
+int orc_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t n, int k)
+{
+    int carries = 0;
+    for (int64_t i = 0; i < n; i++) out[i] = a[i];
+    for (int it = 0; it < k; it++) carries += orc_add(out, b, out, n);
+    return carries;
+}
+
+void orc_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t n)
+{
+    uint64_t *t1 = malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t *t2 = malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t *t3 = malloc(sizeof(uint64_t) * (size_t)n);
+    orc_mul_lo(a, n, a, n, n, t1);   /* a a */
+    orc_add(t1, b, t1, n);           /* a a + b */
+    orc_mul_lo(b, n, b, n, n, t2);   /* b b */
+    orc_add(t2, b, t2, n);           /* b b + b */
+    orc_mul_lo(t1, n, t2, n, n, t3); /* (a a + b)(b b + b) */
+    orc_mul_lo(a, n, b, n, n, out);  /* a b */
+    orc_add(out, t3, out, n);        /* ... + a b */
+    free(t1);
+    free(t2);
+    free(t3);
+}
+
 /* ------------------------------------------------------------------------
  * Batched drivers.
  * ---------------------------------------------------------------------- */

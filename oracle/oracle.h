@@ -75,6 +75,17 @@ int orc_step(int64_t h, int64_t m, const uint64_t *v, int64_t nv,
  * Sec. V-C, Fig. 6 (prec). */
 int64_t orc_prec(const uint64_t *x, int64_t n);
 
+/* The add chain r = a + b + ... + b (k additions), each addition mod B^n as
+ * orc_add; returns the number of carries out (floor((a + k b) / B^n)).
+ * Sec. VI, Table I (6-Add is k = 6). */
+int orc_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t n, int k);
+
+/* Poly = (a a + b) (b b + b) + a b, every product and sum kept to n limbs
+ * (mod B^n, as the paper's same-width multiply and add), into out[0..n).
+ * Sec. VI, Table II: four multiplications (orc_mul_lo) and three additions
+ * (orc_add), in that order. */
+void orc_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t n);
+
 /* ---- batched drivers (uniform batches, instance-major), OpenMP over
  * instances when built with OpenMP.  Each returns the number of host
  * threads it used.  They exist to time the oracle as the CPU baseline. */

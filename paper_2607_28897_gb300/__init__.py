@@ -18,6 +18,7 @@ __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "divmod_noalloc", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
     "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host",
+    "add_chain", "poly", "poly_workspace_bytes",
     "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
     "MAX_LIMBS", "MUL_MAX_LIMBS",
 ]
@@ -61,6 +62,9 @@ SIGNATURES = {
     "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
     "bigint_check_timeout": ([], ctypes.c_int),
     "bigint_host_workspace": ([ctypes.c_int, _I64, _I32, _I32], _SZ),
+    "bigint_add_chain": ([_P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "bigint_poly_workspace": ([_I64, _I32], _SZ),
+    "bigint_poly": ([_P, _P, _P, _I64, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_add_host": ([_P, _P, _P, _P, _I64, _I32, _P, _SZ], ctypes.c_int),
     "bigint_sub_host": ([_P, _P, _P, _P, _I64, _I32, _P, _SZ], ctypes.c_int),
     "bigint_mul_host": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ], ctypes.c_int),
@@ -261,6 +265,39 @@ def shinv(v, h: int, nw: int, w=None, status=None, workspace=None, stream=None):
                              _stream_ptr(stream))
     _check(rc, "bigint_shinv")
     return w, status
+
+
+# ---- fused programs (Sec. VI, Tables I and II) -------------------------------
+def add_chain(a, b, k: int, out=None, carry=None, stream=None):
+    """a + b + ... + b (k additions mod B^n, intermediates in registers);
+    carry = floor((a + k b) / B^n) per instance (uint8) if given."""
+    torch = _torch()
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, n = a.shape
+    out = _empty_like_limbs(a, count, n) if out is None else _dev_tensor(out, "out")
+    rc = load().bigint_add_chain(a.data_ptr(), b.data_ptr(), out.data_ptr(),
+                                 carry.data_ptr() if carry is not None else None, count, n, k,
+                                 _stream_ptr(stream))
+    _check(rc, "bigint_add_chain")
+    return out
+
+
+def poly_workspace_bytes(count: int, n: int) -> int:
+    return int(load().bigint_poly_workspace(count, n))
+
+
+def poly(a, b, out=None, workspace=None, stream=None):
+    """(a a + b)(b b + b) + a b mod B^n per instance, one fused launch."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, n = a.shape
+    out = _empty_like_limbs(a, count, n) if out is None else _dev_tensor(out, "out")
+    if workspace is None:
+        workspace = _workspace(poly_workspace_bytes(count, n), a.device)
+    rc = load().bigint_poly(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, n,
+                            workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                            _stream_ptr(stream))
+    _check(rc, "bigint_poly")
+    return out
 
 
 # ---- host-buffer entry points (copies overlapped with the kernels) ----------

@@ -15,6 +15,12 @@ int mul_max_limbs();
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
+int programs_take_timeout();
+int launch_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry,
+                     int64_t count, int n, int k, cudaStream_t st);
+size_t poly_workspace(int64_t count, int n);
+int launch_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                void *ws, size_t bytes, cudaStream_t st);
 size_t host_workspace(int op, int64_t chunk, int na, int nb);
 int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
              void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes);
@@ -214,9 +220,31 @@ int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64
 }
 
 int bigint_check_timeout(void) {
-  const int a = tc_take_timeout(), b = div_take_timeout();
-  if (a == BIGINT_ECUDA || b == BIGINT_ECUDA) return BIGINT_ECUDA;
-  return a != BIGINT_OK ? a : b;
+  const int a = tc_take_timeout(), b = div_take_timeout(), c = programs_take_timeout();
+  if (a == BIGINT_ECUDA || b == BIGINT_ECUDA || c == BIGINT_ECUDA) return BIGINT_ECUDA;
+  return a != BIGINT_OK ? a : (b != BIGINT_OK ? b : c);
+}
+
+int bigint_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
+                     int64_t count, int32_t n, int32_t k, void *stream) {
+  int rc = check_addsub(a, b, out, count, n);
+  if (rc != BIGINT_OK) return rc;
+  if (k < 1 || k > 255) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  return launch_add_chain(a, b, out, carry_out, count, n, k, as_stream(stream));
+}
+
+size_t bigint_poly_workspace(int64_t count, int32_t n) {
+  if (count < 0 || n < 1 || n > BIGINT_MUL_MAX_LIMBS) return 0;
+  return poly_workspace(count, n);
+}
+
+int bigint_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int32_t n,
+                void *workspace, size_t bytes, void *stream) {
+  if (count < 0 || count > 0x7fffffff || n < 1 || n > BIGINT_MUL_MAX_LIMBS) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!a || !b || !out || !workspace) return BIGINT_EINVAL;
+  return launch_poly(a, b, out, count, n, workspace, bytes, as_stream(stream));
 }
 
 int bigint_mul_variant_for(int32_t na, int32_t nb) {

@@ -1,0 +1,233 @@
+// programs.cu -- fused multi-operation programs per instance (Sec. VI,
+// Tables I and II): the whole program runs in one launch, intermediates stay
+// on chip (registers) or in a per-CTA scratch region that stays in L2, so
+// global-memory traffic is that of one operation.
+//
+//   add chain:  r = a + b + ... + b  (k additions, k = 6 is Table I's 6-Add),
+//               each a full carry-propagating addition mod B^n; carry_out is
+//               the number of wrap-arounds, floor((a + k b) / B^n).
+//   poly:       r = (a a + b) (b b + b) + a b  mod B^n  (Table II's Poly: four
+//               multiplications and three additions, every value kept to n
+//               limbs as the paper's same-width multiply and add do).
+#include "divcore.cuh"
+
+namespace bigint {
+
+// ---------------------------------------------------------------------------
+// Carry into this thread's segment when every thread holds a segment of
+// consecutive limbs in thread order with (generate, propagate) = (g, p) and
+// the block gets carry cin; *cout = carry out of the last thread.  The scan
+// of Fig. 3 with warp ballots, then across warps (blk_addsub's resolve).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t blk_segment_carry(uint32_t g, uint32_t p, uint32_t cin,
+                                                      uint32_t *sm, uint32_t *cout) {
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const WarpCarry wc = warp_gp(g, p);
+  if (lane == 0) {
+    sm[warp] = warp_carry_out(wc, 0);
+    sm[32 + warp] = warp_all_propagate(wc);
+  }
+  __syncthreads();
+  const uint32_t gw = (int)lane < nwarps ? sm[lane] : 0;
+  const uint32_t pw = (int)lane < nwarps ? sm[32 + lane] : 1;
+  const uint64_t cm = warp_carries(warp_gp(gw, pw), cin);
+  const uint32_t cwarp = (uint32_t)(cm >> warp) & 1u;
+  *cout = (uint32_t)(cm >> nwarps) & 1u;
+  const uint64_t lc = warp_carries(wc, cwarp);
+  __syncthreads();  // sm is reused by the next call
+  return (uint32_t)(lc >> lane) & 1u;
+}
+
+// One CTA per instance; thread t holds limbs [t L, t L + L) of the running
+// sum and of b in registers for all k additions.
+template <int L>
+__global__ void __launch_bounds__(1024)
+    k_add_chain(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
+                uint64_t *__restrict__ Out, uint8_t *carry_out, int n, int k) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  const int64_t inst = blockIdx.x;
+  const uint64_t *a = A + inst * (int64_t)n, *b = Bm + inst * (int64_t)n;
+  uint64_t *o = Out + inst * (int64_t)n;
+  const int base = (int)threadIdx.x * L;
+  int nv = n - base;
+  nv = nv < 0 ? 0 : (nv > L ? L : nv);
+  uint64_t r[L], y[L];
+#pragma unroll
+  for (int j = 0; j < L; j++) {
+    r[j] = j < nv ? a[base + j] : 0ull;
+    y[j] = j < nv ? b[base + j] : 0ull;
+  }
+  uint32_t total = 0;
+  for (int it = 0; it < k; it++) {
+    uint32_t c = 0, all_ones = 1;
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      if (j < nv) {
+        const uint64_t t = r[j] + y[j];
+        const uint64_t t2 = t + c;
+        c = (uint32_t)(t < r[j]) | (uint32_t)(t2 < t);
+        r[j] = t2;
+        all_ones &= (uint32_t)(t2 == ~0ull);
+      }
+    }
+    // a segment past the end passes carries through
+    const uint32_t g = nv > 0 ? c : 0u, p = nv > 0 ? (c == 0u && all_ones) : 1u;
+    uint32_t cout;
+    uint32_t cin = blk_segment_carry(g, p, 0u, scr, &cout);
+#pragma unroll
+    for (int j = 0; j < L; j++) {
+      if (j < nv && cin) {
+        r[j] += 1;
+        cin = r[j] == 0 ? 1u : 0u;
+      }
+    }
+    total += cout;
+  }
+#pragma unroll
+  for (int j = 0; j < L; j++)
+    if (j < nv) o[base + j] = r[j];
+  if (carry_out && threadIdx.x == 0) carry_out[inst] = (uint8_t)total;
+}
+
+// ---------------------------------------------------------------------------
+// Poly: persistent CTAs; per instance four low-part products (tensor cores
+// when n >= TC_DIV_MIN, else blk_mul) and three in-place additions through a
+// per-CTA scratch of 3n limbs.
+// ---------------------------------------------------------------------------
+template <bool TC, int G>
+__global__ void __launch_bounds__(512, 1)
+    k_poly(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
+           uint64_t *__restrict__ Out, int n, int64_t count, uint64_t *scratch, int smem_words) {
+  extern __shared__ __align__(1024) uint32_t smem[];
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  __shared__ tcm::TcShared tsh;
+  tcm::TcCtx tcc;
+  if constexpr (TC) tcm::tc_init<256>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
+  uint64_t *T1 = scratch + (int64_t)blockIdx.x * 3 * n, *T2 = T1 + n, *T3 = T2 + n;
+  auto prod = [&](const uint64_t *x, const uint64_t *y, uint64_t *out) {
+    if constexpr (TC) {
+      tcm::tc_product<256, G>(tcc, x, n, y, n, out, n, 0);
+    } else {
+      blk_mul_call<divc::DRB, divc::DQ, divc::DF>(x, n, y, n, out, n, smem, 0);
+    }
+  };
+  auto add_into = [&](uint64_t *t, const uint64_t *u) {  // t = t + u mod B^n
+    auto load = [&](int j) { return make_ulonglong2(t[j], u[j]); };
+    auto store = [&](int j, uint64_t v) { t[j] = v; };
+    blk_addsub<false>(n, 0u, load, store, scr);
+  };
+  for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const uint64_t *a = A + inst * (int64_t)n, *b = Bm + inst * (int64_t)n;
+    uint64_t *o = Out + inst * (int64_t)n;
+    prod(a, a, T1);
+    add_into(T1, b);
+    prod(b, b, T2);
+    add_into(T2, b);
+    prod(T1, T2, T3);
+    prod(a, b, o);
+    add_into(o, T3);
+    __syncthreads();
+    if constexpr (TC) {
+      if (tcc.aborted) break;
+    }
+  }
+  if constexpr (TC) tcm::tc_release<256>(tcc);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+int launch_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry,
+                     int64_t count, int n, int k, cudaStream_t st) {
+  if (count == 0) return BIGINT_OK;
+  if (n <= 8 * 1024) {
+    const int T = ((n + 7) / 8 + 31) / 32 * 32;
+    k_add_chain<8><<<(unsigned)count, T, 0, st>>>(a, b, out, carry, n, k);
+  } else {
+    const int T = ((n + 15) / 16 + 31) / 32 * 32;
+    k_add_chain<16><<<(unsigned)count, T, 0, st>>>(a, b, out, carry, n, k);
+  }
+  return bigint_launch_status();
+}
+
+namespace {
+
+template <bool TC, int G>
+int poly_dyn_max() {
+  static int dyn = -1;
+  if (dyn < 0) {
+    int dev = 0, optin = 0;
+    BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+    BIGINT_CUDA_TRY(
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_poly<TC, G>));
+    const int d = optin - (int)fa.sharedSizeBytes;
+    BIGINT_CUDA_TRY(
+        cudaFuncSetAttribute(k_poly<TC, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+    dyn = d;
+  }
+  return dyn;
+}
+
+int sm_count(int *sms) {
+  int dev = 0;
+  BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+  BIGINT_CUDA_TRY(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+  return BIGINT_OK;
+}
+
+template <bool TC, int G>
+int launch_poly_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                        void *ws, size_t bytes, size_t need, cudaStream_t st) {
+  const int dyn = poly_dyn_max<TC, G>();
+  if (dyn <= 0 || need > (size_t)dyn) return BIGINT_EINVAL;
+  int sms = 0;
+  const int rc = sm_count(&sms);
+  if (rc != BIGINT_OK) return rc;
+  const int64_t grid = count < sms ? count : sms;
+  if (bytes < (size_t)grid * 3 * n * 8) return BIGINT_ENOMEM;
+  k_poly<TC, G><<<(unsigned)grid, 512, need, st>>>(a, b, out, n, count,
+                                                   static_cast<uint64_t *>(ws), (int)(need / 4));
+  return bigint_launch_status();
+}
+
+}  // namespace
+
+// BIGINT_ETIMEOUT if a Poly launch's tensor-core product hit a wait limit
+// since the last call (synchronises the device), else BIGINT_OK.
+int programs_take_timeout() {
+  BIGINT_CUDA_TRY(cudaDeviceSynchronize());
+  int v = 0;
+  BIGINT_CUDA_TRY(cudaMemcpyFromSymbol(&v, tcm::g_timeout, sizeof(int)));
+  if (v) {
+    const int zero = 0;
+    BIGINT_CUDA_TRY(cudaMemcpyToSymbol(tcm::g_timeout, &zero, sizeof(int)));
+    return BIGINT_ETIMEOUT;
+  }
+  return BIGINT_OK;
+}
+
+size_t poly_workspace(int64_t count, int n) {
+  int sms = 0;
+  if (sm_count(&sms) != BIGINT_OK) return 0;
+  const int64_t grid = count < sms ? count : sms;
+  return (size_t)(grid > 0 ? grid : 1) * 3 * (size_t)n * 8;
+}
+
+int launch_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                void *ws, size_t bytes, cudaStream_t st) {
+  if (count == 0) return BIGINT_OK;
+  if (n >= divc::TC_DIV_MIN) {
+    const size_t n8 = tcm::layout<256, 8>(n, n).total, n4 = tcm::layout<256, 4>(n, n).total;
+    if (poly_dyn_max<true, 8>() > 0 && n8 <= (size_t)poly_dyn_max<true, 8>())
+      return launch_poly_variant<true, 8>(a, b, out, count, n, ws, bytes, n8, st);
+    return launch_poly_variant<true, 4>(a, b, out, count, n, ws, bytes, n4, st);
+  }
+  const size_t need = 4 * (size_t)blk_mul_smem_words<divc::DRB, divc::DQ>(n, n);
+  return launch_poly_variant<false, 8>(a, b, out, count, n, ws, bytes, need, st);
+}
+
+}  // namespace bigint

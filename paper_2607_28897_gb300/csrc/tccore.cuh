@@ -204,12 +204,15 @@ __device__ __forceinline__ void tmem_ld_wait() {
 // Recoded digits e[k] at positions lo + k (k = 0..7) of the n-limb number v:
 // e = sext(byte(pos)) + top_bit(byte(pos - 1)); bytes outside [0, 8n) are 0,
 // so position 8n carries the top bit of the last byte and later ones are 0.
+// Plain (coherent) loads: inside the division and program kernels an operand
+// can be a value the same CTA wrote earlier in the launch (a Newton iterate
+// in a reused buffer), which the non-coherent read-only path may not see.
 __device__ __forceinline__ void digits8(const uint64_t *v, int n, int64_t lo, int (&e)[8]) {
   const int64_t p = lo - 1;
   const int64_t la = p >> 3;  // floor
   const int sh = (int)(p & 7) * 8;
-  const uint64_t A = (la >= 0 && la < n) ? __ldg(v + la) : 0ull;
-  const uint64_t B = (la + 1 >= 0 && la + 1 < n) ? __ldg(v + la + 1) : 0ull;
+  const uint64_t A = (la >= 0 && la < n) ? v[la] : 0ull;
+  const uint64_t B = (la + 1 >= 0 && la + 1 < n) ? v[la + 1] : 0ull;
   const uint64_t w = sh ? (A >> sh) | (B << (64 - sh)) : A;  // bytes p .. p+7
   const uint32_t b8 = (uint32_t)(B >> sh) & 0xFFu;           // byte p+8
 #pragma unroll
@@ -272,11 +275,23 @@ __device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, 
 // TMEM column dtm, then a commit to mbar.  For block e only the columns of
 // the tile that meet x (c - e in [0, mx)) are computed, widened to multiples
 // of 16; the group's first MMA overwrites the accumulator if it spans the
-// whole tile, otherwise a clearing MMA with a zero A operand comes first.
+// group's columns (group_span), otherwise a clearing MMA with a zero A
+// operand over those columns comes first.
+// Tile columns [lo, hi) (multiples of 16) that the MMAs of blocks ea..eb
+// write: block e meets columns [max(c0, e), min(c0 + W, e + mx)), both ends
+// growing with e.
+__device__ __forceinline__ void group_span(int c0, int W, int ea, int eb, int mx, int &lo,
+                                           int &hi) {
+  lo = ((c0 > ea ? c0 : ea) - c0) & ~15;
+  hi = ((c0 + W < eb + mx ? c0 + W : eb + mx) - c0 + 15) & ~15;
+}
+
 __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t xs_a,
                                             uint32_t z_a, uint32_t lbo_b, int c0, int W, int ea,
                                             int eb, int mx, uint32_t mbar) {
   tc_fence_after();
+  int slo, shi;
+  group_span(c0, W, ea, eb, mx, slo, shi);
   bool first = true;
   for (int e = ea; e <= eb; e++) {
     const int ca = (c0 > e ? c0 : e) - c0;
@@ -286,13 +301,13 @@ __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t 
     const uint32_t aa = ha + (uint32_t)(16 * (eb - e)) * 128u;
     const uint32_t ba = xs_a + (uint32_t)(c0 + lo - e + 16) * 16u;
     uint32_t accf = 1;
-    if (first) {
+    if (first) {  // columns outside the span are neither written nor drained
       first = false;
-      if (lo == 0 && hi == W) {
+      if (lo == slo && hi == shi) {
         accf = 0;
       } else {
-        mma_f16(dtm, sdesc(z_a, 128, 128), sdesc(xs_a, lbo_b, 128),
-                IDESC_M128 | ((uint32_t)(W >> 3) << 17), 0);
+        mma_f16(dtm + (uint32_t)slo, sdesc(z_a, 128, 128), sdesc(xs_a, lbo_b, 128),
+                IDESC_M128 | ((uint32_t)((shi - slo) >> 3) << 17), 0);
       }
     }
     // K steps of 16 digits: A moves by 2 core matrices (256 bytes), B by two
@@ -309,13 +324,14 @@ __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t 
   mma_commit(mbar);
 }
 
-// Adds the accumulator (this warp's 32 lanes, its 64-column slice) to the
-// thread's int32 column sums; the values are integers below 2^24.
-__device__ __forceinline__ void drain(uint32_t taddr, int cq, int W, int (&acc)[64]) {
+// Adds the accumulator (this warp's 32 lanes, its 64-column slice, the
+// group's columns [lo, hi)) to the thread's int32 column sums; the values
+// are integers of magnitude at most 2^24.
+__device__ __forceinline__ void drain(uint32_t taddr, int cq, int lo, int hi, int (&acc)[64]) {
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     const int col = 64 * cq + 16 * k;
-    if (col < W) {
+    if (col >= lo && col < hi) {
       uint32_t r[16];
       tmem_ld16(taddr + (uint32_t)col, r);
       tmem_ld_wait();
@@ -458,7 +474,9 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           c.phase ^= 1u << ob;
           c.pending &= ~(1u << ob);
           tc_fence_after();
-          drain(t_lane + (uint32_t)(ob * NT), cq, W, acc);
+          int slo, shi;
+          group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
+          drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
         }
         if (gi + 1 < NG) {
           const int na = ea + G, nb2 = na + G - 1 < e_hi ? na + G - 1 : e_hi;
@@ -473,7 +491,11 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
       c.phase ^= 1u << lb;
       c.pending &= ~(1u << lb);
       tc_fence_after();
-      drain(t_lane + (uint32_t)(lb * NT), cq, W, acc);
+      {
+        int slo, shi;
+        group_span(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
+        drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
+      }
       tc_fence_before();
       if (__syncthreads_or(bad)) { c.aborted = true; return false; }
     }

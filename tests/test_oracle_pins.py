@@ -354,3 +354,28 @@ def test_batches_match_single(orc):
         assert st[i] == 0
         assert to_int(q[i]) == to_int(u[i]) // to_int(v[i])
         assert to_int(r[i]) == to_int(u[i]) % to_int(v[i])
+
+
+# ---- fused programs (Sec. VI, Tables I and II) ------------------------------
+@pytest.mark.parametrize("n,k", [(1, 1), (1, 6), (3, 6), (17, 6), (64, 13), (5, 255)])
+def test_add_chain_vs_python_int(orc, n, k):
+    """a + k b mod B^n and floor((a + k b) / B^n): random and all-ones
+    operands (the carry count reaches k)."""
+    rng = random.Random(100 * n + k)
+    for av, bv in ((rng.getrandbits(64 * n), rng.getrandbits(64 * n)),
+                   (B ** n - 1, B ** n - 1), (B ** n - 1, 1), (0, 0)):
+        out, c = orc.add_chain(from_int(av, n), from_int(bv, n), k)
+        s = av + k * bv
+        assert to_int(out) == s % (B ** n)
+        assert c == s // (B ** n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33])
+def test_poly_vs_python_int(orc, n):
+    """(a a + b)(b b + b) + a b mod B^n: every product and sum reduced mod
+    B^n gives the residue of the exact polynomial."""
+    rng = random.Random(7 * n)
+    for av, bv in ((rng.getrandbits(64 * n), rng.getrandbits(64 * n)),
+                   (B ** n - 1, B ** n - 1), (1, 0), (0, B ** n - 1)):
+        out = orc.poly(from_int(av, n), from_int(bv, n))
+        assert to_int(out) == ((av * av + bv) * (bv * bv + bv) + av * bv) % (B ** n)
