@@ -45,10 +45,10 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sizes", default=",".join(str(n) for n in SWEEP))
-    p.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving"],
+    p.add_argument("--workload", default="sweep", choices=["sweep", "batched", "serving", "programs"],
                    help="sweep: the headline step (default); batched: the ragged mixed-op "
                         "batch in one persistent launch vs one launch per size class; "
                         "serving: continuous batching vs per-request launches")
@@ -190,7 +190,8 @@ def cpu_model() -> str:
 # --------------------------------------------------------------------------
 # committed ncu traffic of the multiply kernel, valid only for its source
 # --------------------------------------------------------------------------
-def kernel_source_hash(files=("tcmul.cu", "mul.cu", "blockops.cuh", "common.cuh")) -> str:
+def kernel_source_hash(files=("tccore.cuh", "tcmul.cu", "mul.cu", "blockops.cuh",
+                              "common.cuh")) -> str:
     h = hashlib.sha256()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_2607_28897_gb300", "csrc", f), "rb").read())
@@ -269,6 +270,8 @@ def main():
     if args.workload == "batched":
         run_batched(args)
         return
+    if args.workload == "programs":
+        return run_programs(args)
     if args.workload == "serving":
         run_serving(args)
         return
@@ -546,16 +549,24 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
         h2d += (hu.numel() + hv.numel()) * 8
         d2h += (hq.numel() + hr.numel()) * 8 + 4 * batch
 
+    calls_ms = {}
+
+    def timed(name, fn):
+        c0 = time.perf_counter()
+        fn()
+        calls_ms[name] = calls_ms.get(name, 0.0) + (time.perf_counter() - c0) * 1e3
+
     def step():
         for n in sizes:
             ha, hb, hsa, hsb = host_in[n]
             hs, hd, hp, hc = host_out[n]
-            bi.add_host(ha, hb, out=hs, carry=hc, workspace=ws[n])
-            bi.sub_host(hsa, hsb, out=hd, borrow=hc, workspace=ws[n])
-            bi.mul_host(ha, hb, out=hp, workspace=ws[n])
+            timed(f"add_{n}", lambda: bi.add_host(ha, hb, out=hs, carry=hc, workspace=ws[n]))
+            timed(f"sub_{n}", lambda: bi.sub_host(hsa, hsb, out=hd, borrow=hc, workspace=ws[n]))
+            timed(f"mul_{n}", lambda: bi.mul_host(ha, hb, out=hp, workspace=ws[n]))
         for n, _ in DIV:
             hu, hv, hq, hr, hst, wsd = hdiv[n]
-            bi.divmod_host(hu, hv, q=hq, r=hr, status=hst, workspace=wsd)
+            timed(f"divmod_{2 * n}_{n}",
+                  lambda: bi.divmod_host(hu, hv, q=hq, r=hr, status=hst, workspace=wsd))
 
     # the host link's copy rate on this machine (differs between machines),
     # measured outside the timed region on 512 MiB pinned buffers
@@ -579,6 +590,7 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    calls_ms.clear()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
@@ -589,7 +601,8 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "path": "bigint_*_host (C ABI, pinned host buffers, copies overlapped with kernels)",
-            "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
+            "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
+            "calls_ms": {k: round(v / steps, 2) for k, v in calls_ms.items()}}
 
 def run_batched(args):
     """The batched form: ragged instances (sizes log-uniform over 2^15..2^19
@@ -645,6 +658,65 @@ def run_batched(args):
             "per_class_ms": t_class, "persistent_ms": t_pers, "persistent_tuned_graph_ms": t_graph,
             "tuned_threads": threads, "speedup_vs_per_class": t_class / t_graph,
             "results_identical_across_forms": same}
+    print(json.dumps(line), flush=True)
+
+
+def run_programs(args):
+    """Tables I and II of Sec. VI on the sweep shapes (2^32 bits per operand
+    array): 1-Add vs the fused 6-Add (GB/s over the 3 n 8 bytes one addition
+    must move), and the full product (1-Mul) vs the fused Poly
+    (a a + b)(b b + b) + a b mod B^n (ms per launch), CUDA events, best of
+    the timed repetitions."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+
+    bi.load()
+    sizes = [int(x) for x in args.sizes.split(",")]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def best_of(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return min(times)
+
+    reps = max(args.steps, 1)
+    rows = []
+    for n in sizes:
+        b = sweep_batch(n)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(n)
+        a = torch.randint(-2**62, 2**62, (b, n), dtype=torch.int64, device="cuda", generator=g)
+        y = torch.randint(-2**62, 2**62, (b, n), dtype=torch.int64, device="cuda", generator=g)
+        s = torch.empty_like(a)
+        c = torch.empty(b, dtype=torch.uint8, device="cuda")
+        bytes_ = 24.0 * b * n
+        t1 = best_of(lambda: bi.add(a, y, out=s, carry=c), reps)
+        t6 = best_of(lambda: bi.add_chain(a, y, 6, out=s, carry=c), reps)
+        p = torch.empty((b, 2 * n), dtype=torch.int64, device="cuda")
+        tm = best_of(lambda: bi.mul(a, y, out=p), reps)
+        del p
+        ws = torch.empty(bi.poly_workspace_bytes(b, n), dtype=torch.uint8, device="cuda")
+        tp = best_of(lambda: bi.poly(a, y, out=s, workspace=ws), reps)
+        rows.append({"limbs": n, "batch": b, "add1_GBs": bytes_ / (t1 * 1e-3) / 1e9,
+                     "add6_GBs": bytes_ / (t6 * 1e-3) / 1e9, "mul_full_ms": tm, "poly_ms": tp,
+                     "poly_over_mul": tp / tm})
+        del a, y, s, c, ws
+    line = {"metric": "fused programs: 6-Add GB/s and Poly ms (Tables I, II shapes)",
+            "value": min(r["add6_GBs"] / r["add1_GBs"] for r in rows), "unit": "6-Add/1-Add",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "2^32 bits per operand array at 2^15..2^19 bits; 6-Add = a + 6 b "
+                                   "(six fused additions), Poly = (a a + b)(b b + b) + a b mod B^n"},
+            "rows": rows}
     print(json.dumps(line), flush=True)
 
 
