@@ -254,10 +254,11 @@ __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, i
 // Hankel core matrices of the group whose last block is eb: matrix j, row r,
 // element w = recoded y digit at 128 eb + 127 - 8 j - r - w.
 template <int G>
-__device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, int eb) {
+__device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, int eb, int t0,
+                                        int nthreads) {
   constexpr int HB = hankel_blocks(G);
   const int64_t ytop = 128ll * eb + 127;
-  for (int row = threadIdx.x; row < HB * 8; row += blockDim.x) {
+  for (int row = t0; row < HB * 8; row += nthreads) {
     const int j = row >> 3, r = row & 7;
     const int64_t yhi = ytop - 8 * j - r;
     int e[8];
@@ -363,7 +364,7 @@ struct TcCtx {
   bool aborted;       // a wait hit its limit: no further products
 };
 
-// All threads of the CTA (blockDim = 2 NT): barriers and TMEM (warp 0).
+// All threads of the CTA: barriers and TMEM (warp 0).
 template <int NT>
 __device__ void tc_init(TcCtx &c, uint8_t *sm, TcShared *sh, uint32_t *scr) {
   c.sm = sm;
@@ -403,7 +404,8 @@ __device__ void tc_release(TcCtx &c) {
   if (threadIdx.x < 32) tmem_dealloc(c.tmem, 2 * NT);
 }
 
-// out[0..nout) = low nout limbs of x * y, by the whole CTA (blockDim = 2 NT),
+// out[0..nout) = low nout limbs of x * y, by the whole CTA (blockDim = 2 NT,
+// plus one issuer warp when IW),
 // with nx <= ny, nout <= nx + ny, x, y, out in global memory (out disjoint
 // from x and y) and c.sm holding layout<NT, G>(nx, ny).total bytes.
 //
@@ -414,12 +416,19 @@ __device__ void tc_release(TcCtx &c) {
 // floor(out / B^(h - L0)) is floor(x y / B^h) or one more, and never wraps
 // while x y + B^h < B^nout.
 //
+// IW: one extra warp (the last) only issues MMAs; the issuing thread blocks
+// while the tensor core's queue is full, so on its own warp that wait does
+// not hold up any drain or Hankel build.  Without IW thread 0 issues.
+//
 // Returns false (and sets c.aborted) if a wait hit its limit.
-template <int NT, int G>
+template <int NT, int G, bool IW = false>
 __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, const uint64_t *y,
                                            int ny, uint64_t *out, int nout, int lo) {
-  constexpr int THREADS = 2 * NT;
+  constexpr int DRAIN = 2 * NT;                // threads that drain and build
+  constexpr int THREADS = DRAIN + (IW ? 32 : 0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = IW ? tid == DRAIN : tid == 0;
+  const bool worker = !IW || tid < DRAIN;
   const Layout Ly = layout<NT, G>(nx, ny);
   uint8_t *sm = c.sm;
   const uint32_t sbase = c.sbase;
@@ -457,44 +466,44 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
 #pragma unroll
     for (int i = 0; i < 64; i++) acc[i] = 0;
     if (NG > 0) {
-      build_h<G>(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi);
+      build_h<G>(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid, THREADS);
       fence_async_smem();
       __syncthreads();
       bool bad = false;
       for (int gi = 0; gi < NG; gi++) {
         const int b = gi & 1;
         const int ea = e_lo + gi * G, eb = ea + G - 1 < e_hi ? ea + G - 1 : e_hi;
-        if (tid == 0)
+        if (issuer)
           issue_group(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a, z_a,
                       lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
         c.pending |= 1u << b;
         if (gi >= 1) {  // group gi-1 used the other buffers
           const int ob = b ^ 1;
-          if (!mbar_wait(mb[ob], (c.phase >> ob) & 1u)) bad = true;
+          if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) bad = true;
           c.phase ^= 1u << ob;
           c.pending &= ~(1u << ob);
           tc_fence_after();
           int slo, shi;
           group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
-          drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
+          if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
         }
-        if (gi + 1 < NG) {
+        if (gi + 1 < NG && worker) {
           const int na = ea + G, nb2 = na + G - 1 < e_hi ? na + G - 1 : e_hi;
-          build_h<G>(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2);
+          build_h<G>(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2, tid, DRAIN);
         }
         tc_fence_before();
         fence_async_smem();
         if (__syncthreads_or(bad)) { c.aborted = true; return false; }
       }
       const int lb = (NG - 1) & 1;
-      if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) bad = true;
+      if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) bad = true;  // all: TMEM reuse below
       c.phase ^= 1u << lb;
       c.pending &= ~(1u << lb);
       tc_fence_after();
       {
         int slo, shi;
         group_span(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
-        drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
+        if (worker) drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
       }
       tc_fence_before();
       if (__syncthreads_or(bad)) { c.aborted = true; return false; }

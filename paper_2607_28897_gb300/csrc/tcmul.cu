@@ -9,8 +9,9 @@
 namespace bigint {
 namespace tcm {
 
+// 2 NT drain threads plus one issuer warp (tc_product<NT, G, true>).
 template <int NT, int G>
-__global__ void __launch_bounds__(2 * NT, 256 / NT)
+__global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
              uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -19,7 +20,7 @@ __global__ void __launch_bounds__(2 * NT, 256 / NT)
   TcCtx c;
   tc_init<NT>(c, sm, &sh, scr);
   for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x)
-    if (!tc_product<NT, G>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
+    if (!tc_product<NT, G, true>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
                            Out + inst * (int64_t)nout, nout, 0))
       break;
   tc_release<NT>(c);
@@ -94,7 +95,7 @@ static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_
   BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t slots = (int64_t)sms * (256 / NT);  // CTAs resident at once
   const int64_t grid = count < slots ? count : slots;
-  tcm::k_mul_tc<NT, G><<<(unsigned)grid, 2 * NT, smem, st>>>(x, y, out, nx, ny, nout, count);
+  tcm::k_mul_tc<NT, G><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(x, y, out, nx, ny, nout, count);
   return bigint_launch_status();
 }
 
