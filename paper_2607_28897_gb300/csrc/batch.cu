@@ -67,11 +67,11 @@ __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uin
   }
 }
 
-// TC: 512 threads holding the SM's tensor memory; products with a shorter
-// operand of TC_DIV_MIN limbs or more (multiplications, and the products
-// inside divisions) run on the tensor cores.
+// TC: tcm::TC_CTA_THREADS threads holding the SM's tensor memory; products
+// with a shorter operand of TC_DIV_MIN limbs or more (multiplications, and
+// the products inside divisions) run on the tensor cores.
 template <bool TC>
-__global__ void __launch_bounds__(BATCH_MAX_THREADS)
+__global__ void __launch_bounds__(TC ? tcm::TC_CTA_THREADS : BATCH_MAX_THREADS)
     k_batch(const OpDev *__restrict__ ops, const int32_t *__restrict__ order, int first,
             int count, const uint64_t *in, uint64_t *out, int32_t *status, uint64_t *ws,
             int64_t ws_per_cta, int *queue, int smem_words) {
@@ -184,7 +184,7 @@ int g_batch_threads = 0;  // tuned CTA size of persistent launches (0: from the 
 
 struct Launch {
   int first, count, threads, ctas, smem_words;
-  bool tc;  // k_batch<true>: 512 threads, one CTA per SM, tensor-core products
+  bool tc;  // k_batch<true>: TC_CTA_THREADS threads, one CTA per SM, tensor-core products
 };
 
 }  // namespace
@@ -281,7 +281,7 @@ int batch_configure(bigint_batch *B) {
   P.tc = tc;
   if (tc) {
     P.smem_words = std::min(std::max(words, tc_words), max_words_tc);
-    P.threads = BATCH_MAX_THREADS;
+    P.threads = tcm::TC_CTA_THREADS;
   } else {
     P.smem_words = std::min(words, max_words);
     P.threads = B->threads_override
@@ -316,7 +316,7 @@ int batch_configure(bigint_batch *B) {
     L.count = (int)(j - i);
     L.tc = ltc;
     L.smem_words = ltc ? std::min(std::max(w, tw), max_words_tc) : std::min(w, max_words);
-    L.threads = ltc ? BATCH_MAX_THREADS : threads_for_units(u);
+    L.threads = ltc ? tcm::TC_CTA_THREADS : threads_for_units(u);
     rc = occupancy(L.tc, L.threads, L.smem_words, &per_sm);
     if (rc != BIGINT_OK) return rc;
     L.ctas = std::min(L.count, B->sms * per_sm);

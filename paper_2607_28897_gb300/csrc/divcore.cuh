@@ -122,13 +122,14 @@ __device__ Work carve(uint64_t *base, int nu, int nv, int h) {
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core product inside a division kernel of 512 threads holding 512
-// TMEM columns (tccore.cuh), as one out-of-line copy.
+// Tensor-core product inside a kernel of tcm::TC_CTA_THREADS threads holding
+// 512 TMEM columns (tccore.cuh; the last warp issues the MMAs), as one
+// out-of-line copy.
 // ---------------------------------------------------------------------------
 template <int G>
 __device__ __noinline__ bool tc_call(tcm::TcCtx *c, const uint64_t *x, int nx, const uint64_t *y,
                                      int ny, uint64_t *out, int nout, int lo) {
-  return tcm::tc_product<256, G>(*c, x, nx, y, ny, out, nout, lo);
+  return tcm::tc_product<256, G, true>(*c, x, nx, y, ny, out, nout, lo);
 }
 
 // out[0..nout) = x * y on the tensor cores when the shorter operand has

@@ -38,11 +38,12 @@ using namespace divc;
 // Thread cap per product variant: 512 gives the wide-chunk variant 128
 // registers (no spills in its products); the small variant keeps a 640 cap,
 // whose 96-register budget fits two blocks of ~320 threads on one SM.  The
-// tensor-core variant (TC) runs exactly 512 threads and holds all 512 TMEM
-// columns of its SM: products with a shorter operand of TC_DIV_MIN limbs or
-// more run on the tensor cores (tccore.cuh), smaller ones on blk_mul.
+// tensor-core variant (TC) runs exactly tcm::TC_CTA_THREADS threads and holds
+// all 512 TMEM columns of its SM: products with a shorter operand of
+// TC_DIV_MIN limbs or more run on the tensor cores (tccore.cuh), smaller
+// ones on blk_mul.
 template <int Q, bool TC> constexpr int div_max_threads() {
-  return TC ? 512 : (Q >= 16 ? 512 : 640);
+  return TC ? tcm::TC_CTA_THREADS : (Q >= 16 ? 512 : 640);
 }
 
 template <int RB, int Q, int F, bool TC>
@@ -184,7 +185,7 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
   if (need < smem_words) smem_words = need;
   int T;
   if (TC) {
-    T = 512;
+    T = tcm::TC_CTA_THREADS;
   } else {
     const int units = blk_mul_units<RB, Q>(H < 8192 ? H : 8192, H < 8192 ? H : 8192);
     constexpr int TMAX = div_max_threads<Q, TC>();

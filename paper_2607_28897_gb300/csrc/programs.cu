@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024)
 // per-CTA scratch of 3n limbs.
 // ---------------------------------------------------------------------------
 template <bool TC, int G>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(TC ? tcm::TC_CTA_THREADS : 512, 1)
     k_poly(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
            uint64_t *__restrict__ Out, int n, int64_t count, uint64_t *scratch, int smem_words) {
   extern __shared__ __align__(1024) uint32_t smem[];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(512, 1)
   uint64_t *T1 = scratch + (int64_t)blockIdx.x * 3 * n, *T2 = T1 + n, *T3 = T2 + n;
   auto prod = [&](const uint64_t *x, const uint64_t *y, uint64_t *out) {
     if constexpr (TC) {
-      tcm::tc_product<256, G>(tcc, x, n, y, n, out, n, 0);
+      tcm::tc_product<256, G, true>(tcc, x, n, y, n, out, n, 0);
     } else {
       blk_mul_call<divc::DRB, divc::DQ, divc::DF>(x, n, y, n, out, n, smem, 0);
     }
@@ -189,7 +189,7 @@ int launch_poly_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int
   if (rc != BIGINT_OK) return rc;
   const int64_t grid = count < sms ? count : sms;
   if (bytes < (size_t)grid * 3 * n * 8) return BIGINT_ENOMEM;
-  k_poly<TC, G><<<(unsigned)grid, 512, need, st>>>(a, b, out, n, count,
+  k_poly<TC, G><<<(unsigned)grid, TC ? tcm::TC_CTA_THREADS : 512, need, st>>>(a, b, out, n, count,
                                                    static_cast<uint64_t *>(ws), (int)(need / 4));
   return bigint_launch_status();
 }

@@ -364,6 +364,10 @@ struct TcCtx {
   bool aborted;       // a wait hit its limit: no further products
 };
 
+// Threads of a CTA running tc_product<256, G, true>: 16 drain warps and one
+// issuer warp.
+constexpr int TC_CTA_THREADS = 2 * 256 + 32;
+
 // All threads of the CTA: barriers and TMEM (warp 0).
 template <int NT>
 __device__ void tc_init(TcCtx &c, uint8_t *sm, TcShared *sh, uint32_t *scr) {
