@@ -304,9 +304,9 @@ def poly(a, b, out=None, workspace=None, stream=None):
 def _host_tensor(x, name: str):
     torch = _torch()
     if not isinstance(x, torch.Tensor) or x.device.type != "cpu" or x.dim() != 2:
-        raise BigIntError(f"{name}: expected a 2-D CPU tensor of limbs (pinned for overlap)")
+        raise BigIntError(EINVAL, f"{name}: expected a 2-D CPU tensor of limbs (pinned for overlap)")
     if x.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)) or not x.is_contiguous():
-        raise BigIntError(f"{name}: expected a contiguous int64/uint64 tensor")
+        raise BigIntError(EINVAL, f"{name}: expected a contiguous int64/uint64 tensor")
     return x
 
 

@@ -7,9 +7,15 @@
 // accumulators in tensor memory), exactly:
 //
 //  * Digits.  Each operand is read as base-256 digits (its bytes) recoded to
-//    signed digits e_i = sext(d_i) + top_bit(d_(i-1)) in [-128, 128], plus one
-//    extra digit e_(8n) = top_bit(d_(8n-1)) in {0, 1}; sum e_i 256^i is the
-//    operand again.  Every digit is an exact fp16 value and every digit
+//    signed digits e_i = sext(d_i) + top_bit(d_(i-1)) in [-128, 128] plus
+//    the carry digit e_(8n) = top_bit(d_(8n-1)) in {0, 1}; sum e_i 256^i is
+//    the operand again.  y's carry digit falls in the last Toeplitz block y
+//    already has; x's costs an extra block of 128 digits, so with XC =
+//    false x goes without it: its digits spell x_s = x - t_x B^nx (t_x its
+//    top bit), an nx-limb x fills exactly nx/16 blocks (a 1024-limb product
+//    has 128 output columns, not 129, and fits the two-CTA tile), and
+//    x y = x_s y + t_x y B^nx is restored by one carry-scan addition at the
+//    end when t_x = 1.  Every digit is an exact fp16 value and every digit
 //    product is at most 2^14 in magnitude.
 //  * Blocks.  Output coefficients are grouped in columns of 128 (column c
 //    holds s = 128 c + t).  With x cut into blocks of 128 digits,
@@ -82,19 +88,19 @@ constexpr uint32_t IDESC_M128 = (1u << 4) | ((uint32_t)(128 >> 4) << 24);
 static __device__ int g_timeout = 0;
 
 struct Layout {
-  int mx;    // x blocks of 128 digits (8 nx + 1 digits)
+  int mx;    // x blocks of 128 digits (8 nx digits, + the carry digit if XC)
   int ey;    // last Toeplitz block index of y (e in [0, ey])
   int ctot;  // output columns with nonzero coefficients: mx + ey
   int ptot;  // stored x blocks (16 zero blocks on each side)
   uint32_t xs, z, h0, h1, cs, his, total;  // byte offsets in dynamic shared memory
 };
 
-template <int NT, int G>
+template <int NT, int G, bool XC = true>
 __host__ __device__ inline Layout layout(int nx, int ny) {
   constexpr int HB = hankel_blocks(G);
   Layout L;
-  L.mx = (8 * nx + 1 + 127) / 128;
-  L.ey = (8 * ny + 127) / 128;
+  L.mx = (8 * nx + (XC ? 1 : 0) + 127) / 128;
+  L.ey = (8 * ny + 127) / 128;  // block e meets y digits 128 e - 127 .. 128 e + 127
   L.ctot = L.mx + L.ey;
   L.ptot = L.mx + 32;
   L.xs = 0;
@@ -203,10 +209,12 @@ __device__ __forceinline__ void tmem_ld_wait() {
 // ---- digits ----------------------------------------------------------------
 // Recoded digits e[k] at positions lo + k (k = 0..7) of the n-limb number v:
 // e = sext(byte(pos)) + top_bit(byte(pos - 1)); bytes outside [0, 8n) are 0,
-// so position 8n carries the top bit of the last byte and later ones are 0.
+// so position 8n carries the top bit of the last byte (if CARRY; without it
+// the digits spell v - top_bit(v) B^n) and later positions are 0.
 // Plain (coherent) loads: inside the division and program kernels an operand
 // can be a value the same CTA wrote earlier in the launch (a Newton iterate
 // in a reused buffer), which the non-coherent read-only path may not see.
+template <bool CARRY>
 __device__ __forceinline__ void digits8(const uint64_t *v, int n, int64_t lo, int (&e)[8]) {
   const int64_t p = lo - 1;
   const int64_t la = p >> 3;  // floor
@@ -219,7 +227,7 @@ __device__ __forceinline__ void digits8(const uint64_t *v, int n, int64_t lo, in
   for (int k = 0; k < 8; k++) {
     const uint32_t d = k < 7 ? (uint32_t)(w >> (8 * (k + 1))) & 0xFFu : b8;
     const int c = (int)((w >> (8 * k + 7)) & 1u);
-    e[k] = (int)(int8_t)(uint8_t)d + c;
+    e[k] = (CARRY || lo + k < 8ll * n) ? (int)(int8_t)(uint8_t)d + c : 0;
   }
 }
 
@@ -236,12 +244,13 @@ __device__ __forceinline__ uint32_t pack_h2(int lo, int hi) {
 
 // x blocks p in [-16, mx + 16) into the B layout (chunk (p, h) = digits
 // 128 p + 8 h .. + 8, stored at ((p + 16) + h ptot) * 16).
+template <bool XC>
 __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, int ptot) {
   for (int idx = threadIdx.x; idx < 16 * ptot; idx += blockDim.x) {
     const int h = idx / ptot, pp = idx - h * ptot;
     const int64_t L = 16ll * (pp - 16) + h;
     int e[8];
-    digits8(x, nx, 8 * L, e);
+    digits8<XC>(x, nx, 8 * L, e);
     uint4 v;
     v.x = pack_h2(e[0], e[1]);
     v.y = pack_h2(e[2], e[3]);
@@ -262,7 +271,7 @@ __device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, 
     const int j = row >> 3, r = row & 7;
     const int64_t yhi = ytop - 8 * j - r;
     int e[8];
-    digits8(y, ny, yhi - 7, e);  // e[k] = digit yhi - 7 + k; element w = e[7 - w]
+    digits8<true>(y, ny, yhi - 7, e);  // e[k] = digit yhi - 7 + k; element w = e[7 - w]
     uint4 v;
     v.x = pack_h2(e[7], e[6]);
     v.y = pack_h2(e[5], e[4]);
@@ -425,7 +434,7 @@ __device__ void tc_release(TcCtx &c) {
 // not hold up any drain or Hankel build.  Without IW thread 0 issues.
 //
 // Returns false (and sets c.aborted) if a wait hit its limit.
-template <int NT, int G, bool IW = false>
+template <int NT, int G, bool IW = false, bool XC = true>
 __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, const uint64_t *y,
                                            int ny, uint64_t *out, int nout, int lo) {
   constexpr int DRAIN = 2 * NT;                // threads that drain and build
@@ -433,7 +442,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = IW ? tid == DRAIN : tid == 0;
   const bool worker = !IW || tid < DRAIN;
-  const Layout Ly = layout<NT, G>(nx, ny);
+  const Layout Ly = layout<NT, G, XC>(nx, ny);
   uint8_t *sm = c.sm;
   const uint32_t sbase = c.sbase;
   const uint32_t xs_a = sbase + Ly.xs, z_a = sbase + Ly.z;
@@ -447,7 +456,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
 
   for (int i = tid; i < ZB * 128 / 16; i += THREADS)
     reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
-  fill_x(sm + Ly.xs, x, nx, Ly.ptot);
+  fill_x<XC>(sm + Ly.xs, x, nx, Ly.ptot);
   if (tid == 0) { c.sh->carry_hi = 0; c.sh->carry = 0; }
   fence_async_smem();
   __syncthreads();
@@ -562,6 +571,22 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
     };
     auto store = [&](int j, uint64_t v) { o[j] = v; };
     blk_addsub<true>(nout - L0, 0u, load, store, c.scr);
+    // without x's carry digit the digits spelled x_s = x - t_x B^nx:
+    // x y = x_s y + t_x y B^nx.  In band mode the part of the correction
+    // below L0 is dropped (its carry into L0 is within the band's margin).
+    const uint32_t tx = XC ? 0u : (uint32_t)(x[nx - 1] >> 63);
+    auto add_shifted = [&](int off, const uint64_t *src, int nsrc) {
+      const int st = off > L0 ? off : L0;
+      if (st >= nout) return;
+      uint64_t *oo = out + st;
+      auto ld = [&](int j) {
+        const int k = st + j - off;
+        return make_ulonglong2(oo[j], k < nsrc ? src[k] : 0ull);
+      };
+      auto sto = [&](int j, uint64_t v) { oo[j] = v; };
+      blk_addsub<false>(nout - st, 0u, ld, sto, c.scr);
+    };
+    if (tx) add_shifted(nx, y, ny);
   }
   __syncthreads();
   return true;

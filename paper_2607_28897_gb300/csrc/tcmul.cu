@@ -10,7 +10,8 @@ namespace bigint {
 namespace tcm {
 
 // 2 NT drain threads plus one issuer warp (tc_product<NT, G, true>).
-template <int NT, int G>
+// 2 NT drain threads plus one issuer warp (tc_product<NT, G, true, XC>).
+template <int NT, int G, bool XC>
 __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
              uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count) {
@@ -20,8 +21,8 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
   TcCtx c;
   tc_init<NT>(c, sm, &sh, scr);
   for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x)
-    if (!tc_product<NT, G, true>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
-                           Out + inst * (int64_t)nout, nout, 0))
+    if (!tc_product<NT, G, true, XC>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
+                                     Out + inst * (int64_t)nout, nout, 0))
       break;
   tc_release<NT>(c);
 }
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <int NT, int G>
+template <int NT, int G, bool XC>
 static int tc_dyn_max() {
   static int dyn = -1;
   if (dyn < 0) {
@@ -41,37 +42,38 @@ static int tc_dyn_max() {
         cudaSuccess)
       return 0;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>) != cudaSuccess) return 0;
     const int d = optin - (int)fa.sharedSizeBytes;
-    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             d) != cudaSuccess)
+    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT, G, XC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d) != cudaSuccess)
       return 0;
     dyn = d;
   }
   return dyn;
 }
 
-// Tile width for an nx x ny product (nx <= ny): 128 columns while the
-// output has at most 128 columns of 128 digits (n up to ~1000 limbs for
-// square products), else 256.
-static int tc_tile(int nx, int ny) {
-  return (8 * nx + 1 + 127) / 128 + (8 * ny + 127) / 128 <= 128 ? 128 : 256;
+// The kernel shape of an nx x ny product (nx <= ny).  Output columns of 128
+// digits: ctot = mx + ey.  A product whose columns fit 128 runs the 128-column
+// tile, two CTAs per SM; one that fits only without x's carry digit (square
+// products of 1024 limbs: 129 -> 128 columns) drops it (XC = false: one
+// correction addition); larger ones run the 256-column tile, one CTA per SM.
+// (A 64-column tile with four CTAs per SM measured slower at 512 limbs: each
+// CTA then has 4 warps to build a group's full set of Hankel matrices; and
+// dropping the carry digit where the tile does not change costs 1-4 %.)
+enum TcShape { TC_128_XC, TC_128_NOXC, TC_256 };
+
+static TcShape tc_shape(int nx, int ny) {
+  const int ey = (8 * ny + 127) / 128;
+  if ((8 * nx + 1 + 127) / 128 + ey <= 128) return TC_128_XC;
+  if ((8 * nx + 127) / 128 + ey <= 128) return TC_128_NOXC;
+  return TC_256;
 }
 
-template <int NT, int G>
+template <int NT, int G, bool XC>
 static size_t tc_smem(int nx, int ny) {
-  const tcm::Layout L = tcm::layout<NT, G>(nx, ny);
-  const int d = tc_dyn_max<NT, G>();
+  const tcm::Layout L = tcm::layout<NT, G, XC>(nx, ny);
+  const int d = tc_dyn_max<NT, G, XC>();
   return d > 0 && L.total <= (uint32_t)d ? L.total : 0;
-}
-
-// Group size: 8 Toeplitz blocks per drain where the Hankel buffers fit,
-// else 4 (0: the product does not fit at all).
-template <int NT>
-static int tc_group(int nx, int ny) {
-  if (tc_smem<NT, 8>(nx, ny)) return 8;
-  if (tc_smem<NT, 4>(nx, ny)) return 4;
-  return 0;
 }
 
 // Dynamic shared memory the tensor-core product of an na x nb product
@@ -79,15 +81,20 @@ static int tc_group(int nx, int ny) {
 size_t mul_tc_smem(int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
   if (nx < 1 || ny > 16383) return 0;
-  if (tc_tile(nx, ny) == 128)
-    return tc_group<128>(nx, ny) == 8 ? tc_smem<128, 8>(nx, ny) : tc_smem<128, 4>(nx, ny);
-  return tc_group<256>(nx, ny) == 8 ? tc_smem<256, 8>(nx, ny) : tc_smem<256, 4>(nx, ny);
+  switch (tc_shape(nx, ny)) {
+    case TC_128_XC: return tc_smem<128, 8, true>(nx, ny);
+    case TC_128_NOXC: return tc_smem<128, 8, false>(nx, ny);
+    default: {
+      const size_t s8 = tc_smem<256, 8, true>(nx, ny);
+      return s8 ? s8 : tc_smem<256, 4, true>(nx, ny);
+    }
+  }
 }
 
-template <int NT, int G>
+template <int NT, int G, bool XC>
 static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_t count, int nx,
                      int ny, int nout, cudaStream_t st) {
-  const size_t smem = tc_smem<NT, G>(nx, ny);
+  const size_t smem = tc_smem<NT, G, XC>(nx, ny);
   if (smem == 0) return BIGINT_EINVAL;
   if (count == 0) return BIGINT_OK;
   int dev = 0, sms = 0;
@@ -95,7 +102,8 @@ static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_
   BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t slots = (int64_t)sms * (256 / NT);  // CTAs resident at once
   const int64_t grid = count < slots ? count : slots;
-  tcm::k_mul_tc<NT, G><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(x, y, out, nx, ny, nout, count);
+  tcm::k_mul_tc<NT, G, XC><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(x, y, out, nx, ny, nout,
+                                                                     count);
   return bigint_launch_status();
 }
 
@@ -105,11 +113,13 @@ int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
   int nx = na, ny = nb;
   if (nb < na) { x = b; y = a; nx = nb; ny = na; }
   if (nx < 1 || ny > 16383 || nout < 1 || nout > na + nb) return BIGINT_EINVAL;
-  if (tc_tile(nx, ny) == 128)
-    return tc_group<128>(nx, ny) == 8 ? launch_tc<128, 8>(x, y, out, count, nx, ny, nout, st)
-                                      : launch_tc<128, 4>(x, y, out, count, nx, ny, nout, st);
-  return tc_group<256>(nx, ny) == 8 ? launch_tc<256, 8>(x, y, out, count, nx, ny, nout, st)
-                                    : launch_tc<256, 4>(x, y, out, count, nx, ny, nout, st);
+  switch (tc_shape(nx, ny)) {
+    case TC_128_XC: return launch_tc<128, 8, true>(x, y, out, count, nx, ny, nout, st);
+    case TC_128_NOXC: return launch_tc<128, 8, false>(x, y, out, count, nx, ny, nout, st);
+    default:
+      return tc_smem<256, 8, true>(nx, ny) ? launch_tc<256, 8, true>(x, y, out, count, nx, ny, nout, st)
+                                           : launch_tc<256, 4, true>(x, y, out, count, nx, ny, nout, st);
+  }
 }
 
 // BIGINT_ETIMEOUT if a tensor-core product hit a wait limit since the last

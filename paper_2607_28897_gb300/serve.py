@@ -21,7 +21,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, BATCH_PERSISTENT, OP_DIVMOD, OP_MUL, load, divmod as _divmod, mul as _mul
+from . import Batch, BATCH_PERSISTENT, OP_DIVMOD, OP_MUL, load, op_dtype, divmod as _divmod, mul as _mul
 from . import inputs
 
 
@@ -182,3 +182,140 @@ def run_per_request(w: Workload, limit: int | None = None):
     return {"requests": n, "seconds": total, "throughput": n / total,
             "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+
+class Server:
+    """Request-level API over the batched form: ``submit(op, a, b)`` returns
+    a ticket, ``poll(ticket)`` says whether its result is ready, ``wait``
+    returns it as device tensors (``(product,)`` for OP_MUL, ``(q, r)`` for
+    OP_DIVMOD, ``(sum,)`` / ``(difference,)`` for OP_ADD / OP_SUB; results
+    stay on the device until the caller copies them).
+
+    Pending requests are launched as one ragged batch (persistent form, one
+    launch) when a stream slot is free and the batch's operand, result and
+    workspace bytes fit the HBM budget next to the batches in flight
+    (admission; a request that alone exceeds the budget is refused with
+    BigIntError).  Batches on different streams overlap on the GPU."""
+
+    def __init__(self, budget_bytes: int = 64 << 30, streams: int = 3, max_batch: int = 2048,
+                 device="cuda"):
+        import torch
+
+        load()
+        self.budget = budget_bytes
+        self.max_batch = max_batch
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self._next_stream = 0
+        self._pending = []   # (ticket, op, a, b)
+        self._inflight = []  # dicts: tickets, event, bytes, keep-alive tensors
+        self._done = {}      # ticket -> tuple of result tensors
+        self._ticket = 0
+        self._in_use = 0
+
+    @staticmethod
+    def _out_limbs(op, na, nb):
+        if op == OP_MUL:
+            return na + nb, 0
+        if op == OP_DIVMOD:
+            return max(na - nb + 1, 1), nb
+        return na, 0
+
+    def submit(self, op: int, a, b) -> int:
+        """Queue one operation on 1-D limb tensors (int64/uint64, host or
+        device); returns its ticket."""
+        from . import BigIntError, EINVAL, ENOMEM, OP_ADD, OP_SUB
+
+        if op not in (OP_ADD, OP_SUB, OP_MUL, OP_DIVMOD):
+            raise BigIntError(EINVAL, "submit: unknown op")
+        if a.dim() != 1 or b.dim() != 1:
+            raise BigIntError(EINVAL, "submit: operands must be 1-D limb tensors")
+        if op in (OP_ADD, OP_SUB) and a.numel() != b.numel():
+            raise BigIntError(EINVAL, "submit: add/sub need operands of equal length")
+        o1, o2 = self._out_limbs(op, a.numel(), b.numel())
+        if 8 * (a.numel() + b.numel() + o1 + o2) > self.budget:
+            raise BigIntError(ENOMEM, "submit: request larger than the HBM budget")
+        t = self._ticket
+        self._ticket += 1
+        self._pending.append((t, op, a, b))
+        self._pump()
+        return t
+
+    def _retire(self):
+        still = []
+        for f in self._inflight:
+            if f["event"].query():
+                for t, res in f["results"].items():
+                    self._done[t] = res
+                self._in_use -= f["bytes"]
+            else:
+                still.append(f)
+        self._inflight = still
+
+    def _pump(self):
+        import numpy as np
+        import torch
+
+        self._retire()
+        while self._pending and len(self._inflight) < len(self.streams):
+            take, in_limbs, out_limbs = [], 0, 0
+            for t, op, a, b in self._pending[: self.max_batch]:
+                o1, o2 = self._out_limbs(op, a.numel(), b.numel())
+                add_in, add_out = a.numel() + b.numel(), o1 + o2
+                if take and 8 * (in_limbs + add_in + out_limbs + add_out) + self._in_use > self.budget:
+                    break
+                take.append((t, op, a, b))
+                in_limbs += add_in
+                out_limbs += add_out
+            if 8 * (in_limbs + out_limbs) + self._in_use > self.budget and self._inflight:
+                return  # wait for a batch to retire
+            self._pending = self._pending[len(take):]
+            ops = np.zeros(len(take), dtype=op_dtype())
+            ia = ib = oo = 0
+            pos = 0
+            for k, (t, op, a, b) in enumerate(take):
+                o1, o2 = self._out_limbs(op, a.numel(), b.numel())
+                ops[k] = (op, a.numel(), b.numel(), 0, pos, pos + a.numel(), oo,
+                          oo + o1 if op == OP_DIVMOD else 0)
+                pos += a.numel() + b.numel()
+                oo += o1 + o2
+            s = self.streams[self._next_stream % len(self.streams)]
+            self._next_stream += 1
+            with torch.cuda.stream(s):
+                pool = torch.cat([x.to(self.device, dtype=torch.int64, non_blocking=True).view(-1)
+                                  for _, _, a, b in take for x in (a, b)])
+                out = torch.empty(max(oo, 1), dtype=torch.int64, device=self.device)
+                status = torch.empty(len(take), dtype=torch.int32, device=self.device)
+                batch = Batch(ops, device=self.device, stream=s)
+                batch.launch(pool, out, status, mode=BATCH_PERSISTENT, stream=s)
+                ev = torch.cuda.Event()
+                ev.record(s)
+            results = {}
+            for k, (t, op, a, b) in enumerate(take):
+                o = ops[k]
+                o1, o2 = self._out_limbs(op, a.numel(), b.numel())
+                r1 = out[int(o["o1"]):int(o["o1"]) + o1]
+                results[t] = (r1, out[int(o["o2"]):int(o["o2"]) + o2]) if op == OP_DIVMOD else (r1,)
+            nbytes = 8 * (in_limbs + out_limbs) + batch.workspace_bytes
+            self._in_use += nbytes
+            self._inflight.append({"event": ev, "results": results, "bytes": nbytes,
+                                   "keep": (pool, out, status, batch)})
+
+    def poll(self, ticket: int) -> bool:
+        self._pump()
+        return ticket in self._done
+
+    def wait(self, ticket: int):
+        """The result tensors of a ticket (blocks until its batch is done)."""
+        from . import BigIntError, EINVAL
+
+        while ticket not in self._done:
+            self._pump()
+            if ticket in self._done:
+                break
+            if not self._inflight:
+                if any(t == ticket for t, *_ in self._pending):
+                    continue
+                raise BigIntError(EINVAL, f"wait: unknown ticket {ticket}")
+            self._inflight[0]["event"].synchronize()
+        return self._done.pop(ticket)

@@ -34,3 +34,45 @@ def test_serving_budget_admission():
     w = serve.make_workload(32, 100, rate=50000.0, min_limbs=8, max_limbs=300)
     res = serve.run_continuous(w, budget_bytes=1, streams=2, max_batch=16)
     assert res["requests"] == 100 and not res["status"].any()
+
+
+def test_server_submit_poll_wait(orc):
+    """The request-level API: mixed requests submitted one by one, results
+    (device tensors) equal the oracle's; a tight HBM budget forces several
+    batches; poll reports completion."""
+    import numpy as np
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+    from paper_2607_28897_gb300.serve import Server
+
+    rng = np.random.default_rng(5)
+    srv = Server(budget_bytes=4 << 20, streams=2, max_batch=16)
+    reqs = []
+    for i in range(40):
+        op = (bi.OP_ADD, bi.OP_SUB, bi.OP_MUL, bi.OP_DIVMOD)[i % 4]
+        nb = int(rng.integers(1, 600))
+        na = nb if op in (bi.OP_ADD, bi.OP_SUB) else int(rng.integers(nb, 2 * nb + 1))
+        a = inputs.limbs(1000 + i, 1, na)[0]
+        b = inputs.limbs(2000 + i, 1, nb, top_nonzero=True)[0]
+        ta = torch.from_numpy(a.view(np.int64)).cuda() if i % 2 else torch.from_numpy(a.view(np.int64))
+        tb = torch.from_numpy(b.view(np.int64)).cuda()
+        reqs.append((srv.submit(op, ta, tb), op, a, b))
+    for t, op, a, b in reqs:
+        res = [x.cpu().numpy().view(np.uint64) for x in srv.wait(t)]
+        if op == bi.OP_ADD:
+            assert np.array_equal(res[0], orc.add(a, b)[0])
+        elif op == bi.OP_SUB:
+            assert np.array_equal(res[0], orc.sub(a, b)[0])
+        elif op == bi.OP_MUL:
+            assert np.array_equal(res[0], orc.mul(a, b))
+        else:
+            q, r, _ = orc.divmod_(a, b)
+            assert np.array_equal(res[0], q) and np.array_equal(res[1], r)
+    t = srv.submit(bi.OP_MUL, torch.ones(8, dtype=torch.int64), torch.ones(8, dtype=torch.int64))
+    srv.wait(t)
+    assert not srv.poll(t)  # consumed
+    with pytest.raises(bi.BigIntError):
+        srv.submit(bi.OP_MUL, torch.ones(1 << 20, dtype=torch.int64),
+                   torch.ones(1 << 20, dtype=torch.int64))

@@ -30,7 +30,8 @@ def check(bi, orc, a, b):
 
 @pytest.mark.parametrize("na,nb", [(1, 1), (1, 2), (2, 3), (15, 16), (16, 16), (17, 17),
                                    (33, 40), (64, 64), (100, 37), (255, 257), (512, 512),
-                                   (1000, 999), (2048, 2048), (3001, 17)])
+                                   (1000, 999), (1024, 1024), (1024, 1031), (1017, 1024),
+                                   (2048, 2048), (3001, 17)])
 def test_shapes(bi, orc, na, nb):
     from paper_2607_28897_gb300 import inputs
 
@@ -54,11 +55,12 @@ def test_multi_tile(bi, orc, na, nb):
 @pytest.mark.parametrize("pattern", [0xFFFFFFFFFFFFFFFF, 0x7F807F807F807F80,
                                      0x807F807F807F807F, 0x8080808080808080,
                                      0x7F7F7F7F7F7F7F7F, 0x0000000000000080])
-def test_extreme_digits(bi, orc, pattern):
+@pytest.mark.parametrize("n", [1024, 8192])
+def test_extreme_digits(bi, orc, pattern, n):
     """Byte patterns whose signed digits are all +-128 (alternating 0x7F/0x80)
-    put every accumulator group at its bound 2^22; all-ones and lone top
-    bits exercise the carry digit above the top byte."""
-    n = 8192
+    put every accumulator group at its bound 2^24; all-ones and lone top
+    bits exercise the carry digit above the top byte (1024 limbs: the shape
+    whose x operand goes without it, corrected by t_x y B^nx)."""
     a = np.full((2, n), np.uint64(pattern), dtype=np.uint64)
     b = a.copy()
     b[1] = np.uint64(0xFFFFFFFFFFFFFFFF ^ pattern)
