@@ -511,11 +511,12 @@ def main():
 
 def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, world, dist):
     """Same step through the library's host-buffer entry points
-    (bigint_add_host, _sub_host, _mul_host, _divmod_host): every call copies
-    its inputs from pinned host memory and its results (with carries and
-    statuses) back to pinned host memory inside the timed region; the
-    library overlaps the copies of one chunk with the kernels of the next.
-    Timed on the host clock around synchronous calls."""
+    (bigint_host_async for add, sub, mul and divmod, then bigint_host_sync):
+    every call copies its inputs from pinned host memory and its results
+    (with carries and statuses) back to pinned host memory inside the timed
+    region; the library overlaps the copies of one chunk or call with the
+    kernels of the next.  Timed on the host clock; calls_ms are enqueue
+    times, "sync" the wait for the step's work."""
     steps = max(1, args.e2e_steps)
 
     def pinned_like(t, dtype=None):
@@ -528,11 +529,14 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
         b = S["a"].shape[0]
         host_in[n] = tuple(S[k].cpu().pin_memory() for k in ("a", "b", "sa", "sb"))
         host_out[n] = (pinned_like(S["s"]), pinned_like(S["d"]), pinned_like(S["p"]),
+                       torch.empty(b, dtype=torch.uint8).pin_memory(),
                        torch.empty(b, dtype=torch.uint8).pin_memory())
         chunk = max(1, (b + 3) // 4)
-        nbytes = max(bi.host_workspace_bytes(op, chunk, n, n)
-                     for op in (bi.OP_ADD, bi.OP_SUB, bi.OP_MUL))
-        ws[n] = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        # one workspace per call, so that enqueued calls do not wait for each
+        # other, with a staging slot per chunk (2 x two slots): no chunk waits
+        # for an earlier chunk's copy-out
+        ws[n] = {op: torch.empty(2 * bi.host_workspace_bytes(op, chunk, n, n), dtype=torch.uint8,
+                                 device=dev) for op in (bi.OP_ADD, bi.OP_SUB, bi.OP_MUL)}
         a_bytes = S["a"].numel() * 8
         h2d += 6 * a_bytes  # add: a, b; sub: sa, sb; mul: a, b
         d2h += 2 * a_bytes + 2 * b + S["p"].numel() * 8
@@ -543,7 +547,7 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
         hq, hr = pinned_like(D["q"]), pinned_like(D["r"])
         hst = torch.empty(batch, dtype=torch.int32).pin_memory()
         chunk = max(1, (batch + 3) // 4)
-        wsd = torch.empty(bi.host_workspace_bytes(bi.OP_DIVMOD, chunk, 2 * n, n),
+        wsd = torch.empty(2 * bi.host_workspace_bytes(bi.OP_DIVMOD, chunk, 2 * n, n),
                           dtype=torch.uint8, device=dev)
         hdiv[n] = (hu, hv, hq, hr, hst, wsd)
         h2d += (hu.numel() + hv.numel()) * 8
@@ -557,16 +561,24 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
         calls_ms[name] = calls_ms.get(name, 0.0) + (time.perf_counter() - c0) * 1e3
 
     def step():
+        # every call is enqueued (sync=False): the copies of one call overlap
+        # the kernels of the next; one host_sync ends the step
         for n in sizes:
             ha, hb, hsa, hsb = host_in[n]
-            hs, hd, hp, hc = host_out[n]
-            timed(f"add_{n}", lambda: bi.add_host(ha, hb, out=hs, carry=hc, workspace=ws[n]))
-            timed(f"sub_{n}", lambda: bi.sub_host(hsa, hsb, out=hd, borrow=hc, workspace=ws[n]))
-            timed(f"mul_{n}", lambda: bi.mul_host(ha, hb, out=hp, workspace=ws[n]))
+            hs, hd, hp, hc, hbw = host_out[n]
+            w = ws[n]
+            timed(f"add_{n}", lambda: bi.add_host(ha, hb, out=hs, carry=hc,
+                                                  workspace=w[bi.OP_ADD], sync=False))
+            timed(f"sub_{n}", lambda: bi.sub_host(hsa, hsb, out=hd, borrow=hbw,
+                                                  workspace=w[bi.OP_SUB], sync=False))
+            timed(f"mul_{n}", lambda: bi.mul_host(ha, hb, out=hp, workspace=w[bi.OP_MUL],
+                                                  sync=False))
         for n, _ in DIV:
             hu, hv, hq, hr, hst, wsd = hdiv[n]
             timed(f"divmod_{2 * n}_{n}",
-                  lambda: bi.divmod_host(hu, hv, q=hq, r=hr, status=hst, workspace=wsd))
+                  lambda: bi.divmod_host(hu, hv, q=hq, r=hr, status=hst, workspace=wsd,
+                                         sync=False))
+        timed("sync", bi.host_sync)
 
     # the host link's copy rate on this machine (differs between machines),
     # measured outside the timed region on 512 MiB pinned buffers
@@ -600,7 +612,8 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     dt = ranks.max_over_ranks(time.perf_counter() - t0, dist, dev)
     return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "path": "bigint_*_host (C ABI, pinned host buffers, copies overlapped with kernels)",
+            "path": "bigint_host_async + bigint_host_sync (C ABI, pinned host buffers, copies "
+                    "overlapped with kernels)",
             "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
             "calls_ms": {k: round(v / steps, 2) for k, v in calls_ms.items()}}
 

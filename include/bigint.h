@@ -254,9 +254,12 @@ int bigint_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t cou
  * (its measurements keep data on the device); this is the library's own
  * end-to-end path.
  *
- * bigint_host_workspace: bytes of workspace for chunks of `chunk` instances
- * of op (BIGINT_OP_ADD .. BIGINT_OP_DIVMOD; for divmod na = nu, nb = nv);
- * 0 for invalid arguments. */
+ * bigint_host_workspace: bytes of workspace for two staging slots of
+ * `chunk` instances of op (BIGINT_OP_ADD .. BIGINT_OP_DIVMOD; for divmod
+ * na = nu, nb = nv); 0 for invalid arguments.  A call cuts its batch into
+ * chunks of at most a quarter of the batch (and what two slots of the
+ * given workspace hold) and uses as many slots as the workspace holds, up
+ * to one per chunk and 8: a larger workspace lets more copy-ins run ahead. */
 size_t bigint_host_workspace(int op, int64_t chunk, int32_t na, int32_t nb);
 int bigint_add_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
                     int64_t count, int32_t n, void *workspace, size_t bytes);
@@ -267,6 +270,19 @@ int bigint_mul_host(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t
 int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                        int32_t *status, int64_t count, int32_t nu, int32_t nv,
                        void *workspace, size_t bytes);
+/* The same, enqueued only (returns before the copies and kernels finish, so
+ * the copies of one call overlap the kernels of the next): op is
+ * BIGINT_OP_ADD .. BIGINT_OP_DIVMOD; out0 = result / quotient, out1 = the
+ * remainder (divmod; else unused), aux = carry / borrow bytes (add, sub) or
+ * int32 statuses (divmod), may be NULL; na = nb = n for add and sub.  Host
+ * buffers and the workspace must stay untouched until bigint_host_sync()
+ * returns, which waits for every enqueued call of the current device (and
+ * returns BIGINT_ECUDA if one failed).  Calls that share a workspace are
+ * ordered by the library.                                                   */
+int bigint_host_async(int op, const uint64_t *a, const uint64_t *b, uint64_t *out0,
+                      uint64_t *out1, void *aux, int64_t count, int32_t na, int32_t nb,
+                      void *workspace, size_t bytes);
+int bigint_host_sync(void);
 
 /* ---- tuning and measurement ---------------------------------------------
  * Selects the kernel variant an operation uses from now on (process-wide,

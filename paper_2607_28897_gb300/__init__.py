@@ -17,7 +17,7 @@ import os
 __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "divmod_noalloc", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
-    "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host",
+    "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host", "host_sync",
     "add_chain", "poly", "poly_workspace_bytes",
     "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
     "MAX_LIMBS", "MUL_MAX_LIMBS",
@@ -69,6 +69,9 @@ SIGNATURES = {
     "bigint_sub_host": ([_P, _P, _P, _P, _I64, _I32, _P, _SZ], ctypes.c_int),
     "bigint_mul_host": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ], ctypes.c_int),
     "bigint_divmod_host": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ], ctypes.c_int),
+    "bigint_host_async": ([ctypes.c_int, _P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ],
+                          ctypes.c_int),
+    "bigint_host_sync": ([], ctypes.c_int),
     "bigint_probe_int_throughput": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -326,42 +329,60 @@ def _host_out(count, n, out):
     return torch.empty((count, n), dtype=torch.int64).pin_memory() if out is None else out
 
 
-def add_host(a, b, out=None, carry=None, workspace=None, device="cuda"):
+def _host_call(op, a, b, out0, out1, aux, na, nb, ws, sync, name):
+    count = a.shape[0]
+    args = (a.data_ptr(), b.data_ptr(), out0.data_ptr(),
+            out1.data_ptr() if out1 is not None else None,
+            aux.data_ptr() if aux is not None else None, count, na, nb, ws.data_ptr(),
+            ws.numel() * ws.element_size())
+    if sync:
+        L = load()
+        if op in (OP_ADD, OP_SUB):
+            fn = L.bigint_add_host if op == OP_ADD else L.bigint_sub_host
+            rc = fn(args[0], args[1], args[2], args[4], count, na, args[8], args[9])
+        elif op == OP_MUL:
+            rc = L.bigint_mul_host(args[0], args[1], args[2], count, na, nb, args[8], args[9])
+        else:
+            rc = L.bigint_divmod_host(args[0], args[1], args[2], args[3], args[4], count, na, nb,
+                                      args[8], args[9])
+    else:
+        rc = load().bigint_host_async(op, *args)
+    _check(rc, name)
+
+
+def add_host(a, b, out=None, carry=None, workspace=None, device="cuda", sync=True):
     """a + b for CPU (pinned) tensors: chunks copied in, added and copied
-    back with the copies overlapping the kernels."""
-    return _addsub_host(load().bigint_add_host, OP_ADD, a, b, out, carry, workspace, device)
+    back with the copies overlapping the kernels.  sync=False only enqueues
+    (host_sync() waits)."""
+    return _addsub_host(OP_ADD, a, b, out, carry, workspace, device, sync)
 
 
-def sub_host(a, b, out=None, borrow=None, workspace=None, device="cuda"):
-    return _addsub_host(load().bigint_sub_host, OP_SUB, a, b, out, borrow, workspace, device)
+def sub_host(a, b, out=None, borrow=None, workspace=None, device="cuda", sync=True):
+    return _addsub_host(OP_SUB, a, b, out, borrow, workspace, device, sync)
 
 
-def _addsub_host(fn, op, a, b, out, flag, workspace, device):
-    torch = _torch()
+def _addsub_host(op, a, b, out, flag, workspace, device, sync):
     a, b = _host_tensor(a, "a"), _host_tensor(b, "b")
     count, n = a.shape
     out = _host_tensor(_host_out(count, n, out), "out")
     ws = _host_ws(op, count, n, n, workspace, device)
-    rc = fn(a.data_ptr(), b.data_ptr(), out.data_ptr(), flag.data_ptr() if flag is not None else None,
-            count, n, ws.data_ptr(), ws.numel() * ws.element_size())
-    _check(rc, "bigint_add_host" if op == OP_ADD else "bigint_sub_host")
+    _host_call(op, a, b, out, None, flag, n, n, ws, sync,
+               "bigint_add_host" if op == OP_ADD else "bigint_sub_host")
     return out
 
 
-def mul_host(a, b, out=None, workspace=None, device="cuda"):
+def mul_host(a, b, out=None, workspace=None, device="cuda", sync=True):
     """Full products of CPU (pinned) tensors, copies overlapped with kernels."""
     a, b = _host_tensor(a, "a"), _host_tensor(b, "b")
     count, na = a.shape
     nb = b.shape[1]
     out = _host_tensor(_host_out(count, na + nb, out), "out")
     ws = _host_ws(OP_MUL, count, na, nb, workspace, device)
-    rc = load().bigint_mul_host(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
-                                ws.data_ptr(), ws.numel() * ws.element_size())
-    _check(rc, "bigint_mul_host")
+    _host_call(OP_MUL, a, b, out, None, None, na, nb, ws, sync, "bigint_mul_host")
     return out
 
 
-def divmod_host(u, v, q=None, r=None, status=None, workspace=None, device="cuda"):
+def divmod_host(u, v, q=None, r=None, status=None, workspace=None, device="cuda", sync=True):
     """q, r (and per-instance status) of CPU (pinned) tensors, copies
     overlapped with the division kernels."""
     torch = _torch()
@@ -373,11 +394,13 @@ def divmod_host(u, v, q=None, r=None, status=None, workspace=None, device="cuda"
     if status is None:
         status = torch.empty(count, dtype=torch.int32).pin_memory()
     ws = _host_ws(OP_DIVMOD, count, nu, nv, workspace, device)
-    rc = load().bigint_divmod_host(u.data_ptr(), v.data_ptr(), q.data_ptr(), r.data_ptr(),
-                                   status.data_ptr(), count, nu, nv, ws.data_ptr(),
-                                   ws.numel() * ws.element_size())
-    _check(rc, "bigint_divmod_host")
+    _host_call(OP_DIVMOD, u, v, q, r, status, nu, nv, ws, sync, "bigint_divmod_host")
     return q, r, status
+
+
+def host_sync() -> None:
+    """Waits for every host-buffer call enqueued with sync=False."""
+    _check(load().bigint_host_sync(), "bigint_host_sync")
 
 
 def set_variant(op: int, variant: int) -> None:

@@ -23,7 +23,8 @@ int launch_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t cou
                 void *ws, size_t bytes, cudaStream_t st);
 size_t host_workspace(int op, int64_t chunk, int na, int nb);
 int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
-             void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes);
+             void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes, bool sync);
+int host_sync();
 int div_take_timeout();
 int div_set_variant(int v);
 int batch_set_variant(int v);
@@ -200,24 +201,35 @@ size_t bigint_host_workspace(int op, int64_t chunk, int32_t na, int32_t nb) {
 
 int bigint_add_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,
                     int64_t count, int32_t n, void *workspace, size_t bytes) {
-  return host_run(BIGINT_OP_ADD, a, b, out, nullptr, carry_out, count, n, n, workspace, bytes);
+  return host_run(BIGINT_OP_ADD, a, b, out, nullptr, carry_out, count, n, n, workspace, bytes,
+                  true);
 }
 
 int bigint_sub_host(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *borrow_out,
                     int64_t count, int32_t n, void *workspace, size_t bytes) {
-  return host_run(BIGINT_OP_SUB, a, b, out, nullptr, borrow_out, count, n, n, workspace, bytes);
+  return host_run(BIGINT_OP_SUB, a, b, out, nullptr, borrow_out, count, n, n, workspace, bytes,
+                  true);
 }
 
 int bigint_mul_host(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
                     int32_t na, int32_t nb, void *workspace, size_t bytes) {
-  return host_run(BIGINT_OP_MUL, a, b, out, nullptr, nullptr, count, na, nb, workspace, bytes);
+  return host_run(BIGINT_OP_MUL, a, b, out, nullptr, nullptr, count, na, nb, workspace, bytes,
+                  true);
 }
 
 int bigint_divmod_host(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                        int32_t *status, int64_t count, int32_t nu, int32_t nv,
                        void *workspace, size_t bytes) {
-  return host_run(BIGINT_OP_DIVMOD, u, v, q, r, status, count, nu, nv, workspace, bytes);
+  return host_run(BIGINT_OP_DIVMOD, u, v, q, r, status, count, nu, nv, workspace, bytes, true);
 }
+
+int bigint_host_async(int op, const uint64_t *a, const uint64_t *b, uint64_t *out0,
+                      uint64_t *out1, void *aux, int64_t count, int32_t na, int32_t nb,
+                      void *workspace, size_t bytes) {
+  return host_run(op, a, b, out0, out1, aux, count, na, nb, workspace, bytes, false);
+}
+
+int bigint_host_sync(void) { return host_sync(); }
 
 int bigint_check_timeout(void) {
   const int a = tc_take_timeout(), b = div_take_timeout(), c = programs_take_timeout();

@@ -4,9 +4,14 @@
 // A call splits its batch into chunks and runs three library streams: copy
 // in (host -> device), compute (the uniform-batch kernel of the operation)
 // and copy out (device -> host).  Chunk i uses staging slot i % 2 of the
-// caller's device workspace, so chunk i+1 is copied in while chunk i is
-// computed and chunk i-1 is copied out; events order the three streams per
-// slot.  The call returns when every result is in host memory.  With pinned
+// caller's device workspace (as many slots as it holds, up to one per chunk
+// and MAX_SLOTS), so chunk i+1 is copied in while chunk i is computed and
+// chunk i-1 is copied out; events order the three streams per slot.  The plain call returns when every result is in host memory; the
+// _async form only enqueues, so the copies of one call overlap the kernels
+// of the next, and bigint_host_sync() waits for everything enqueued.  A
+// call's first copy-in waits for every earlier call whose workspace range
+// overlaps its own (a ring of the last calls' ranges and completion events),
+// so calls may share workspaces in any shapes.  With pinned
 // host buffers (cudaHostAlloc / cudaHostRegister) the copies run
 // asynchronously on the copy engines; pageable buffers still give correct
 // results, without the overlap.
@@ -89,11 +94,17 @@ Slot carve_slot(const Shape &s, int64_t c, uint8_t *base) {
 }
 
 // The three streams and the per-slot events of one device (created on first
-// use, kept for the process).
+// use, kept for the process), and the workspace ranges of the last calls
+// with the events that mark their last copy-out.
+constexpr int RING = 16;
+constexpr int MAX_SLOTS = 8;
 struct Pipe {
   bool ready = false;
   cudaStream_t in, comp, out;
-  cudaEvent_t loaded[2], done[2], freed[2];
+  cudaEvent_t loaded[MAX_SLOTS], done[MAX_SLOTS], freed[MAX_SLOTS];
+  cudaEvent_t finished[RING];
+  uintptr_t lo[RING] = {}, hi[RING] = {};  // empty range: never recorded
+  int next = 0;
 };
 Pipe g_pipe[MAX_DEVICES];
 
@@ -106,11 +117,13 @@ int get_pipe(Pipe **pp) {
     BIGINT_CUDA_TRY(cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking));
     BIGINT_CUDA_TRY(cudaStreamCreateWithFlags(&p.comp, cudaStreamNonBlocking));
     BIGINT_CUDA_TRY(cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < MAX_SLOTS; i++) {
       BIGINT_CUDA_TRY(cudaEventCreateWithFlags(&p.loaded[i], cudaEventDisableTiming));
       BIGINT_CUDA_TRY(cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming));
       BIGINT_CUDA_TRY(cudaEventCreateWithFlags(&p.freed[i], cudaEventDisableTiming));
     }
+    for (int i = 0; i < RING; i++)
+      BIGINT_CUDA_TRY(cudaEventCreateWithFlags(&p.finished[i], cudaEventDisableTiming));
     p.ready = true;
   }
   *pp = &p;
@@ -133,7 +146,7 @@ int64_t chunk_size(const Shape &s, int64_t count, size_t bytes) {
 }
 
 int run(const Shape &s, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
-        void *aux, int64_t count, void *workspace, size_t bytes) {
+        void *aux, int64_t count, void *workspace, size_t bytes, bool sync) {
   if (count == 0) return BIGINT_OK;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % ALIGN) != 0) return BIGINT_EINVAL;
   const int64_t c = chunk_size(s, count, bytes);
@@ -142,14 +155,26 @@ int run(const Shape &s, const uint64_t *in0, const uint64_t *in1, uint64_t *out0
   int rc = get_pipe(&p);
   if (rc != BIGINT_OK) return rc;
   uint8_t *ws = static_cast<uint8_t *>(workspace);
-  const Slot slots[2] = {carve_slot(s, c, ws), carve_slot(s, c, ws + slot_bytes(s, c))};
   const int64_t nchunks = (count + c - 1) / c;
+  const size_t sb = slot_bytes(s, c);
+  int64_t ns = (int64_t)(bytes / sb);  // staging slots: >= 2 (chunk_size), <= chunks, <= MAX_SLOTS
+  if (ns > nchunks) ns = nchunks;
+  if (ns > MAX_SLOTS) ns = MAX_SLOTS;
+  if (ns < 1) ns = 1;
+  Slot slots[MAX_SLOTS];
+  for (int64_t k = 0; k < ns; k++) slots[k] = carve_slot(s, c, ws + k * sb);
+  // earlier calls that used any of this call's workspace must be done with it;
+  // the ring entry about to be reused is waited for too (its range is dropped)
+  const uintptr_t wlo = reinterpret_cast<uintptr_t>(ws), whi = wlo + (size_t)ns * sb;
+  for (int e = 0; e < RING; e++)
+    if ((p->lo[e] < whi && wlo < p->hi[e]) || (e == p->next && p->hi[e] > p->lo[e]))
+      BIGINT_CUDA_TRY(cudaStreamWaitEvent(p->in, p->finished[e], 0));
   for (int64_t i = 0; i < nchunks && rc == BIGINT_OK; i++) {
-    const int k = (int)(i & 1);
+    const int k = (int)(i % ns);
     const Slot &sl = slots[k];
     const int64_t i0 = i * c, m = count - i0 < c ? count - i0 : c;
-    // copy in, once the slot's previous results have been copied out
-    if (i >= 2) BIGINT_CUDA_TRY(cudaStreamWaitEvent(p->in, p->freed[k], 0));
+    // copy in, once the slot's previous results (this call) have been copied out
+    if (i >= ns) BIGINT_CUDA_TRY(cudaStreamWaitEvent(p->in, p->freed[k], 0));
     BIGINT_CUDA_TRY(cudaMemcpyAsync(sl.in0, in0 + i0 * s.na, 8 * (size_t)m * s.na,
                                     cudaMemcpyHostToDevice, p->in));
     BIGINT_CUDA_TRY(cudaMemcpyAsync(sl.in1, in1 + i0 * s.nb, 8 * (size_t)m * s.nb,
@@ -184,6 +209,13 @@ int run(const Shape &s, const uint64_t *in0, const uint64_t *in1, uint64_t *out0
                                       (size_t)m * s.aux, cudaMemcpyDeviceToHost, p->out));
     BIGINT_CUDA_TRY(cudaEventRecord(p->freed[k], p->out));
   }
+  if (rc == BIGINT_OK) {  // this call's workspace range is free once its last copy-out is done
+    BIGINT_CUDA_TRY(cudaEventRecord(p->finished[p->next], p->out));
+    p->lo[p->next] = wlo;
+    p->hi[p->next] = whi;
+    p->next = (p->next + 1) % RING;
+  }
+  if (!sync && rc == BIGINT_OK) return BIGINT_OK;
   const cudaError_t e = cudaStreamSynchronize(p->out);
   if (rc != BIGINT_OK) {
     cudaStreamSynchronize(p->comp);
@@ -212,11 +244,20 @@ size_t host_workspace(int op, int64_t chunk, int na, int nb) {
 }
 
 int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
-             void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes) {
+             void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes, bool sync) {
   if (!shape_ok(op, count, na, nb)) return BIGINT_EINVAL;
   if (count > 0 && (!in0 || !in1 || !out0)) return BIGINT_EINVAL;
   if (op == BIGINT_OP_DIVMOD && count > 0 && !out1) return BIGINT_EINVAL;
-  return run(shape_of(op, na, nb), in0, in1, out0, out1, aux, count, workspace, bytes);
+  return run(shape_of(op, na, nb), in0, in1, out0, out1, aux, count, workspace, bytes, sync);
+}
+
+int host_sync() {
+  Pipe *p = nullptr;
+  const int rc = get_pipe(&p);
+  if (rc != BIGINT_OK) return rc;
+  const cudaError_t a = cudaStreamSynchronize(p->in), b = cudaStreamSynchronize(p->comp),
+                    c = cudaStreamSynchronize(p->out);
+  return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess) ? BIGINT_OK : BIGINT_ECUDA;
 }
 
 }  // namespace bigint

@@ -95,3 +95,45 @@ def test_workspace_too_small(bi):
     ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(bi.BigIntError):
         bi.mul_host(a, a, workspace=ws)
+
+
+def test_async_calls_share_a_workspace(bi, orc):
+    """Enqueued calls of different operations and shapes on ONE workspace
+    (each carves it differently), then one host_sync: every result equals
+    the oracle's, so a call never overwrites a region an earlier call still
+    copies out of."""
+    import torch
+    from paper_2607_28897_gb300 import inputs
+
+    n = 256
+    a = inputs.limbs(81, 24, n)
+    b = inputs.limbs(82, 24, n)
+    u = inputs.limbs(83, 24, 2 * n, top_nonzero=True)
+    v = inputs.limbs(84, 24, n, top_nonzero=True)
+    big = max(bi.host_workspace_bytes(op, 3, 2 * n if op == bi.OP_DIVMOD else n, n)
+              for op in (bi.OP_ADD, bi.OP_SUB, bi.OP_MUL, bi.OP_DIVMOD))
+    ws = torch.empty(big, dtype=torch.uint8, device="cuda")
+    ha, hb, hu, hv = host(a), host(b), host(u), host(v)
+    carry = torch.zeros(24, dtype=torch.uint8).pin_memory()
+    borrow = torch.zeros(24, dtype=torch.uint8).pin_memory()
+    outs = []
+    for rep in range(3):
+        s = bi.add_host(ha, hb, carry=carry, workspace=ws, sync=False)
+        d = bi.sub_host(ha, hb, borrow=borrow, workspace=ws, sync=False)
+        p = bi.mul_host(ha, hb, workspace=ws, sync=False)
+        q, r, st = bi.divmod_host(hu, hv, workspace=ws, sync=False)
+        outs.append((s, d, p, q, r, st))
+    bi.host_sync()
+    ws_add = orc.batch_add(a, b)
+    ws_sub = orc.batch_sub(a, b)
+    prod = orc.batch_mul(a, b)
+    oq, orr, _ = orc.batch_divmod(u, v)
+    for s, d, p, q, r, st in outs:
+        assert np.array_equal(s.numpy().view(np.uint64), ws_add[0])
+        assert np.array_equal(d.numpy().view(np.uint64), ws_sub[0])
+        assert np.array_equal(p.numpy().view(np.uint64), prod)
+        assert np.array_equal(q.numpy().view(np.uint64), oq)
+        assert np.array_equal(r.numpy().view(np.uint64), orr)
+        assert not st.numpy().any()
+    assert np.array_equal(carry.numpy(), ws_add[1])
+    assert np.array_equal(borrow.numpy(), ws_sub[1])
