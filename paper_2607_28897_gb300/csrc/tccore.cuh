@@ -261,23 +261,59 @@ __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, i
 }
 
 // Hankel core matrices of the group whose last block is eb: matrix j, row r,
-// element w = recoded y digit at 128 eb + 127 - 8 j - r - w.
+// element w = recoded y digit at 128 eb + 127 - 8 j - r - w.  Row s = 8 j + r
+// is the run D[s .. s + 8) of the reversed digit sequence D[i] = digit at
+// 128 eb + 127 - i, so each digit is recoded once into D and the rows are
+// copied out of it: D is held twice in the staging area (the second copy one
+// element ahead, so that every run starts on a 4-byte boundary in one of
+// them; the copies 16 banks apart).  Thread t <= HB recodes limb
+// 16 eb + 15 - t, i.e. D[8 t .. 8 t + 8), from that limb and the one below;
+// hank_load fetches them (so the loads can be issued ahead of a wait) and
+// hank_build, called by threads 0 .. NTH - 1 (NTH a multiple of 32, named
+// barrier 1), writes D and the rows.
+struct HankLimbs {
+  uint64_t hi, lo;
+};
+
 template <int G>
-__device__ __forceinline__ void build_h(uint8_t *hb, const uint64_t *y, int ny, int eb, int t0,
-                                        int nthreads) {
+__device__ __forceinline__ HankLimbs hank_load(const uint64_t *y, int ny, int eb, int t) {
   constexpr int HB = hankel_blocks(G);
-  const int64_t ytop = 128ll * eb + 127;
-  for (int row = t0; row < HB * 8; row += nthreads) {
-    const int j = row >> 3, r = row & 7;
-    const int64_t yhi = ytop - 8 * j - r;
-    int e[8];
-    digits8<true>(y, ny, yhi - 7, e);  // e[k] = digit yhi - 7 + k; element w = e[7 - w]
-    uint4 v;
-    v.x = pack_h2(e[7], e[6]);
-    v.y = pack_h2(e[5], e[4]);
-    v.z = pack_h2(e[3], e[2]);
-    v.w = pack_h2(e[1], e[0]);
-    *reinterpret_cast<uint4 *>(hb + row * 16) = v;
+  HankLimbs v{0ull, 0ull};
+  if (t <= HB) {
+    const int64_t U = 16ll * eb + 15 - t;
+    if (U >= 0 && U < ny) v.hi = y[U];
+    if (U >= 1 && U - 1 < ny) v.lo = y[U - 1];
+  }
+  return v;
+}
+
+template <int G>
+__host__ __device__ constexpr int hank_stage_words() { return 4 * hankel_blocks(G) + 20; }
+
+template <int G, int NTH>
+__device__ __forceinline__ void hank_build(uint8_t *hb, uint8_t *st, HankLimbs v, int t) {
+  constexpr int HB = hankel_blocks(G);
+  static_assert(HB + 1 <= NTH && NTH % 32 == 0, "one limb per staging thread");
+  static_assert(2 * hank_stage_words<G>() * 4 <= 32 * 128 * 4, "staging fits the column-sum area");
+  uint32_t *D0 = reinterpret_cast<uint32_t *>(st), *D1 = D0 + hank_stage_words<G>();
+  if (t <= HB) {
+    // f[k + 1] = recoded digit k of limb U (k = -1 .. 7): its byte, sign
+    // extended, plus the top bit of the byte below it
+    const uint64_t below = (v.hi << 8) | (v.lo >> 56);
+    int f[9];
+    f[0] = (int)(int8_t)(uint8_t)(v.lo >> 56) + (int)((v.lo >> 55) & 1u);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+      f[k + 1] = (int)(int8_t)(uint8_t)(v.hi >> (8 * k)) + (int)((below >> (8 * k + 7)) & 1u);
+    *reinterpret_cast<uint4 *>(D0 + 4 * t) =
+        make_uint4(pack_h2(f[8], f[7]), pack_h2(f[6], f[5]), pack_h2(f[4], f[3]), pack_h2(f[2], f[1]));
+    *reinterpret_cast<uint4 *>(D1 + 4 * t) =
+        make_uint4(pack_h2(f[7], f[6]), pack_h2(f[5], f[4]), pack_h2(f[3], f[2]), pack_h2(f[1], f[0]));
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(NTH) : "memory");
+  for (int s = t; s < 8 * HB; s += NTH) {
+    const uint32_t *p = ((s & 1) ? D1 : D0) + (s >> 1);
+    *reinterpret_cast<uint4 *>(hb + 16 * s) = make_uint4(p[0], p[1], p[2], p[3]);
   }
 }
 
@@ -479,7 +515,9 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
 #pragma unroll
     for (int i = 0; i < 64; i++) acc[i] = 0;
     if (NG > 0) {
-      build_h<G>(sm + Ly.h0, y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid, THREADS);
+      if (worker)
+        hank_build<G, DRAIN>(sm + Ly.h0, sm + Ly.cs,
+                             hank_load<G>(y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid), tid);
       fence_async_smem();
       __syncthreads();
       bool bad = false;
@@ -490,6 +528,13 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           issue_group(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a, z_a,
                       lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
         c.pending |= 1u << b;
+        // the next group's y limbs are fetched before the wait
+        const bool more = gi + 1 < NG && worker;
+        HankLimbs hv{0ull, 0ull};
+        if (more) {
+          const int na = ea + G;
+          hv = hank_load<G>(y, ny, na + G - 1 < e_hi ? na + G - 1 : e_hi, tid);
+        }
         if (gi >= 1) {  // group gi-1 used the other buffers
           const int ob = b ^ 1;
           if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) bad = true;
@@ -500,10 +545,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
           if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
         }
-        if (gi + 1 < NG && worker) {
-          const int na = ea + G, nb2 = na + G - 1 < e_hi ? na + G - 1 : e_hi;
-          build_h<G>(b ? sm + Ly.h0 : sm + Ly.h1, y, ny, nb2, tid, DRAIN);
-        }
+        if (more) hank_build<G, DRAIN>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
         tc_fence_before();
         fence_async_smem();
         if (__syncthreads_or(bad)) { c.aborted = true; return false; }
