@@ -102,7 +102,7 @@ __host__ __device__ inline Layout layout(int nx, int ny) {
   L.mx = (8 * nx + (XC ? 1 : 0) + 127) / 128;
   L.ey = (8 * ny + 127) / 128;  // block e meets y digits 128 e - 127 .. 128 e + 127
   L.ctot = L.mx + L.ey;
-  L.ptot = L.mx + 32;
+  L.ptot = (L.mx + 32) | 1;  // odd: the 16 h-rows of a warp's x stores hit distinct banks
   L.xs = 0;
   L.z = (uint32_t)L.ptot * 256u;
   L.h0 = L.z + ZB * 128;
@@ -207,56 +207,75 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 // ---- digits ----------------------------------------------------------------
-// Recoded digits e[k] at positions lo + k (k = 0..7) of the n-limb number v:
-// e = sext(byte(pos)) + top_bit(byte(pos - 1)); bytes outside [0, 8n) are 0,
-// so position 8n carries the top bit of the last byte (if CARRY; without it
-// the digits spell v - top_bit(v) B^n) and later positions are 0.
-// Plain (coherent) loads: inside the division and program kernels an operand
-// can be a value the same CTA wrote earlier in the launch (a Newton iterate
-// in a reused buffer), which the non-coherent read-only path may not see.
-template <bool CARRY>
-__device__ __forceinline__ void digits8(const uint64_t *v, int n, int64_t lo, int (&e)[8]) {
-  const int64_t p = lo - 1;
-  const int64_t la = p >> 3;  // floor
-  const int sh = (int)(p & 7) * 8;
-  const uint64_t A = (la >= 0 && la < n) ? v[la] : 0ull;
-  const uint64_t B = (la + 1 >= 0 && la + 1 < n) ? v[la + 1] : 0ull;
-  const uint64_t w = sh ? (A >> sh) | (B << (64 - sh)) : A;  // bytes p .. p+7
-  const uint32_t b8 = (uint32_t)(B >> sh) & 0xFFu;           // byte p+8
-#pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const uint32_t d = k < 7 ? (uint32_t)(w >> (8 * (k + 1))) & 0xFFu : b8;
-    const int c = (int)((w >> (8 * k + 7)) & 1u);
-    e[k] = (CARRY || lo + k < 8ll * n) ? (int)(int8_t)(uint8_t)d + c : 0;
-  }
+// Recoded digit k of a limb (k = 0..7): its byte k sign-extended plus the top
+// bit of byte k - 1 (byte -1 = the top byte of the limb below), so a number
+// of n limbs spells sum_k e_k 256^k with digits in [-128, 128] and a carry
+// digit (the top bit of its last byte) at position 8n.
+// Plain (coherent) loads of the limbs: inside the division and program
+// kernels an operand can be a value the same CTA wrote earlier in the launch
+// (a Newton iterate in a reused buffer), which the non-coherent read-only
+// path may not see.
+//
+// The digits of limb v (below = the limb underneath) as 16-bit lanes biased
+// by 0x6600: lane j of ev is digit 2j, lane j of od digit 2j + 1; dm1 is
+// digit 7 of below (position -1).  Each lane stays in [0x6580, 0x6680], so
+// the lanes of a 64-bit sum never carry into each other.
+struct Digits16 {
+  uint64_t ev, od;
+  uint32_t dm1;
+};
+
+__device__ __forceinline__ Digits16 recode16(uint64_t v, uint64_t below) {
+  constexpr uint64_t LANE = 0x00FF00FF00FF00FFull, TOP = 0x0080008000800080ull;
+  constexpr uint64_t ONE = 0x0001000100010001ull, BIAS = 0x6600660066006600ull;
+  const uint64_t E = v & LANE, O = (v >> 8) & LANE;
+  Digits16 d;
+  d.ev = BIAS + E - ((E & TOP) << 1) + (((O >> 7) & ONE) << 16) + (below >> 63);
+  d.od = BIAS + O - ((O & TOP) << 1) + ((E >> 7) & ONE);
+  const uint32_t b7 = (uint32_t)(below >> 56);
+  d.dm1 = 0x6600u + b7 - ((b7 & 0x80u) << 1) + ((uint32_t)(below >> 55) & 1u);
+  return d;
 }
 
-// Two small integers (|v| <= 512) as an fp16 pair: 1536 + v has ulp 1 in
-// fp16, so its bit pattern is 0x6600 + v, and subtracting 1536 is exact.
-__device__ __forceinline__ uint32_t pack_h2(int lo, int hi) {
-  const uint32_t m = 0x66006600u + (uint32_t)lo + ((uint32_t)hi << 16);
-  const __half2 a = __halves2half2(__ushort_as_half((unsigned short)(m & 0xFFFFu)),
-                                   __ushort_as_half((unsigned short)(m >> 16)));
+// Two biased lanes (0x6600 + v, |v| <= 128) to an fp16 pair: 0x6600 + v is
+// the fp16 pattern of 1536 + v (ulp 1 there), and subtracting 1536 is exact.
+__device__ __forceinline__ uint32_t unbias_h2(uint32_t m) {
+  const __half2 a = *reinterpret_cast<const __half2 *>(&m);
   const __half2 r = __hsub2(a, __half2half2(__ushort_as_half((unsigned short)0x6600u)));
-  return (uint32_t)__half_as_ushort(__low2half(r)) |
-         ((uint32_t)__half_as_ushort(__high2half(r)) << 16);
+  return *reinterpret_cast<const uint32_t *>(&r);
 }
 
-// x blocks p in [-16, mx + 16) into the B layout (chunk (p, h) = digits
-// 128 p + 8 h .. + 8, stored at ((p + 16) + h ptot) * 16).
+// x blocks p in [-16, mx + 16) into the B layout: chunk (p, h) = digits
+// 128 p + 8 h .. + 8 = the digits of limb 16 p + h, stored at
+// ((p + 16) + h ptot) * 16.  Without XC the digits past limb nx - 1 are 0
+// (they spell x - top_bit(x) B^nx).  Thread i takes limb i - 256, so a
+// warp's loads are coalesced; a thread issues the loads of four limbs before
+// it recodes any, so their latencies overlap.
 template <bool XC>
 __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, int ptot) {
-  for (int idx = threadIdx.x; idx < 16 * ptot; idx += blockDim.x) {
-    const int h = idx / ptot, pp = idx - h * ptot;
-    const int64_t L = 16ll * (pp - 16) + h;
-    int e[8];
-    digits8<XC>(x, nx, 8 * L, e);
-    uint4 v;
-    v.x = pack_h2(e[0], e[1]);
-    v.y = pack_h2(e[2], e[3]);
-    v.z = pack_h2(e[4], e[5]);
-    v.w = pack_h2(e[6], e[7]);
-    *reinterpret_cast<uint4 *>(xs + (size_t)idx * 16) = v;
+  constexpr int U = 4;
+  const int total = 16 * ptot, step = (int)blockDim.x;
+  for (int i0 = threadIdx.x; i0 < total; i0 += U * step) {
+    uint64_t v[U], below[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int L = i0 + u * step - 256;
+      v[u] = (L >= 0 && L < nx && L + 256 < total) ? x[L] : 0ull;
+      below[u] = (L >= 1 && L - 1 < nx && (XC || L < nx) && L + 256 < total) ? x[L - 1] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int i = i0 + u * step;
+      if (i < total) {
+        const int pp = i >> 4, h = i & 15;
+        const Digits16 d = recode16(v[u], below[u]);
+        const uint32_t el = (uint32_t)d.ev, eh = (uint32_t)(d.ev >> 32);
+        const uint32_t ol = (uint32_t)d.od, oh = (uint32_t)(d.od >> 32);
+        *reinterpret_cast<uint4 *>(xs + (size_t)(pp + h * ptot) * 16) = make_uint4(
+            unbias_h2(__byte_perm(el, ol, 0x5410)), unbias_h2(__byte_perm(el, ol, 0x7632)),
+            unbias_h2(__byte_perm(eh, oh, 0x5410)), unbias_h2(__byte_perm(eh, oh, 0x7632)));
+      }
+    }
   }
 }
 
@@ -297,18 +316,16 @@ __device__ __forceinline__ void hank_build(uint8_t *hb, uint8_t *st, HankLimbs v
   static_assert(2 * hank_stage_words<G>() * 4 <= 32 * 128 * 4, "staging fits the column-sum area");
   uint32_t *D0 = reinterpret_cast<uint32_t *>(st), *D1 = D0 + hank_stage_words<G>();
   if (t <= HB) {
-    // f[k + 1] = recoded digit k of limb U (k = -1 .. 7): its byte, sign
-    // extended, plus the top bit of the byte below it
-    const uint64_t below = (v.hi << 8) | (v.lo >> 56);
-    int f[9];
-    f[0] = (int)(int8_t)(uint8_t)(v.lo >> 56) + (int)((v.lo >> 55) & 1u);
-#pragma unroll
-    for (int k = 0; k < 8; k++)
-      f[k + 1] = (int)(int8_t)(uint8_t)(v.hi >> (8 * k)) + (int)((below >> (8 * k + 7)) & 1u);
+    // D[8 t + w] = digit 7 - w of limb U; the second copy starts at D[1]
+    const Digits16 d = recode16(v.hi, v.lo);
+    const uint32_t el = (uint32_t)d.ev, eh = (uint32_t)(d.ev >> 32);
+    const uint32_t ol = (uint32_t)d.od, oh = (uint32_t)(d.od >> 32);
     *reinterpret_cast<uint4 *>(D0 + 4 * t) =
-        make_uint4(pack_h2(f[8], f[7]), pack_h2(f[6], f[5]), pack_h2(f[4], f[3]), pack_h2(f[2], f[1]));
+        make_uint4(unbias_h2(__byte_perm(oh, eh, 0x7632)), unbias_h2(__byte_perm(oh, eh, 0x5410)),
+                   unbias_h2(__byte_perm(ol, el, 0x7632)), unbias_h2(__byte_perm(ol, el, 0x5410)));
     *reinterpret_cast<uint4 *>(D1 + 4 * t) =
-        make_uint4(pack_h2(f[7], f[6]), pack_h2(f[5], f[4]), pack_h2(f[3], f[2]), pack_h2(f[1], f[0]));
+        make_uint4(unbias_h2(__byte_perm(eh, oh, 0x5432)), unbias_h2(__byte_perm(eh, ol, 0x7610)),
+                   unbias_h2(__byte_perm(el, ol, 0x5432)), unbias_h2(__byte_perm(el, d.dm1, 0x5410)));
   }
   asm volatile("bar.sync 1, %0;" ::"n"(NTH) : "memory");
   for (int s = t; s < 8 * HB; s += NTH) {

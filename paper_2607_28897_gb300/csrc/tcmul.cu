@@ -1,7 +1,7 @@
 // tcmul.cu -- batched full (and low-part) products on the tensor cores.
 //
-// One persistent CTA per SM (NT = 256) or two (NT = 128) loops over the
-// instances of a uniform batch, each product computed by tc_product
+// Persistent CTAs, one per SM (NT = 256), two (NT = 128) or three (NT = 64),
+// loop over the instances of a uniform batch, each product computed by tc_product
 // (tccore.cuh: the digit convolution as tcgen05 fp16 MMAs with exact fp32
 // accumulation, Sec. V-B's schoolbook product on the tensor cores).
 #include "tccore.cuh"
@@ -9,7 +9,17 @@
 namespace bigint {
 namespace tcm {
 
-// 2 NT drain threads plus one issuer warp (tc_product<NT, G, true>).
+// Asks L2 for the 16-byte-aligned part of [p, p + bytes) (no completion to
+// wait for): the next instance's operands come in from HBM while this one
+// is computed, so its first loads meet L2 rather than HBM.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a))
+                 : "memory");
+}
+
 // 2 NT drain threads plus one issuer warp (tc_product<NT, G, true, XC>).
 template <int NT, int G, bool XC>
 __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
@@ -20,10 +30,16 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   TcCtx c;
   tc_init<NT>(c, sm, &sh, scr);
-  for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x)
+  for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x) {
+    const int64_t next = inst + gridDim.x;
+    if (threadIdx.x == 0 && next < count) {
+      prefetch_l2(X + next * (int64_t)nx, 8 * (size_t)nx);
+      prefetch_l2(Y + next * (int64_t)ny, 8 * (size_t)ny);
+    }
     if (!tc_product<NT, G, true, XC>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
                                      Out + inst * (int64_t)nout, nout, 0))
       break;
+  }
   tc_release<NT>(c);
 }
 
@@ -57,15 +73,22 @@ static int tc_dyn_max() {
 // tile, two CTAs per SM; one that fits only without x's carry digit (square
 // products of 1024 limbs: 129 -> 128 columns) drops it (XC = false: one
 // correction addition); larger ones run the 256-column tile, one CTA per SM.
-// (A 64-column tile with four CTAs per SM measured slower at 512 limbs: each
-// CTA then has 4 warps to build a group's full set of Hankel matrices; and
-// dropping the carry digit where the tile does not change costs 1-4 %.)
-enum TcShape { TC_128_XC, TC_128_NOXC, TC_256 };
+// Products whose columns fit 64 (square products up to 512 limbs, without
+// the carry digit where needed) run a 64-column tile with groups of 7 blocks,
+// three CTAs per SM: at such sizes an MMA's time is set by reading its
+// 4 KB A operand from shared memory rather than by N, and one issuing CTA
+// reaches about two thirds of that rate, so three CTAs keep the tensor core
+// busy while the others drain, build and finish their products.
+// (Dropping the carry digit where the tile does not change costs 1-4 %.)
+enum TcShape { TC_64_XC, TC_64_NOXC, TC_128_XC, TC_128_NOXC, TC_256 };
 
 static TcShape tc_shape(int nx, int ny) {
   const int ey = (8 * ny + 127) / 128;
-  if ((8 * nx + 1 + 127) / 128 + ey <= 128) return TC_128_XC;
-  if ((8 * nx + 127) / 128 + ey <= 128) return TC_128_NOXC;
+  const int cx = (8 * nx + 1 + 127) / 128 + ey, c0 = (8 * nx + 127) / 128 + ey;
+  if (cx <= 64) return TC_64_XC;
+  if (c0 <= 64) return TC_64_NOXC;
+  if (cx <= 128) return TC_128_XC;
+  if (c0 <= 128) return TC_128_NOXC;
   return TC_256;
 }
 
@@ -82,6 +105,8 @@ size_t mul_tc_smem(int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
   if (nx < 1 || ny > 16383) return 0;
   switch (tc_shape(nx, ny)) {
+    case TC_64_XC: return tc_smem<64, 7, true>(nx, ny);
+    case TC_64_NOXC: return tc_smem<64, 7, false>(nx, ny);
     case TC_128_XC: return tc_smem<128, 8, true>(nx, ny);
     case TC_128_NOXC: return tc_smem<128, 8, false>(nx, ny);
     default: {
@@ -100,7 +125,19 @@ static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_
   int dev = 0, sms = 0;
   BIGINT_CUDA_TRY(cudaGetDevice(&dev));
   BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t slots = (int64_t)sms * (256 / NT);  // CTAs resident at once
+  // CTAs resident at once on an SM: TMEM allows 256 / NT, shared memory
+  // per SM / (dynamic + static + the per-block reservation)
+  int smem_sm = 0, reserved = 0;
+  BIGINT_CUDA_TRY(
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  BIGINT_CUDA_TRY(
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  cudaFuncAttributes fa;
+  BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>));
+  int per_sm = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+  if (per_sm > 256 / NT) per_sm = 256 / NT;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t slots = (int64_t)sms * per_sm;
   const int64_t grid = count < slots ? count : slots;
   tcm::k_mul_tc<NT, G, XC><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(x, y, out, nx, ny, nout,
                                                                      count);
@@ -114,6 +151,8 @@ int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
   if (nb < na) { x = b; y = a; nx = nb; ny = na; }
   if (nx < 1 || ny > 16383 || nout < 1 || nout > na + nb) return BIGINT_EINVAL;
   switch (tc_shape(nx, ny)) {
+    case TC_64_XC: return launch_tc<64, 7, true>(x, y, out, count, nx, ny, nout, st);
+    case TC_64_NOXC: return launch_tc<64, 7, false>(x, y, out, count, nx, ny, nout, st);
     case TC_128_XC: return launch_tc<128, 8, true>(x, y, out, count, nx, ny, nout, st);
     case TC_128_NOXC: return launch_tc<128, 8, false>(x, y, out, count, nx, ny, nout, st);
     default:
