@@ -412,6 +412,23 @@ def main():
         breakdown[f"divmod_{2 * n}_{n}"] = {"ms": t, "ops_per_s": batch / (t * 1e-3),
                                             "limb_gops": batch * (n + 1) * n / (t * 1e-3) / 1e9}
 
+    # ---- single-product latency (serving): one product on one CTA against
+    #      its output tiles spread over CTAs (bigint_mul_split)
+    latency = {}
+    for n in (4096, 8192):
+        a1, b1 = sweep[n]["a"][:1], sweep[n]["b"][:1]
+        o1 = torch.empty((1, 2 * n), dtype=torch.int64, device=dev)
+        ws1 = torch.empty(max(1, bi.mul_split_workspace_bytes(1, n, n)), dtype=torch.uint8,
+                          device=dev)
+        row = {"tiles": bi.mul_split_workspace_bytes(1, n, n) // 16}
+        for name, fn in (("mul_us", lambda: bi.mul(a1, b1, out=o1, stream=stream)),
+                         ("mul_split_us", lambda: bi.mul_split(a1, b1, out=o1, workspace=ws1,
+                                                               stream=stream))):
+            for _ in range(3):
+                fn()
+            row[name] = round(time_op(fn, reps=20) * 1e3, 1)
+        latency[f"mul_{n}x{n}_one_product"] = row
+
     # ---- roofline of the dominant kernel: the multiply launch at the largest
     #      size (2^19 bits), the longest launch of the step
     peaks = {}
@@ -502,6 +519,7 @@ def main():
             "data": "synthetic", "config": workload_config(sizes), "roofline": roofline,
             "roofline_add": roofline_add, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
+            "latency": latency,
         }
         print(json.dumps(line), flush=True)
     if dist:

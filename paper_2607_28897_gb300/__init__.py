@@ -15,7 +15,8 @@ import ctypes
 import os
 
 __all__ = [
-    "BigIntError", "load", "add", "sub", "mul", "mul_lo", "divmod", "divmod_noalloc", "shinv",
+    "BigIntError", "load", "add", "sub", "mul", "mul_lo", "mul_split", "mul_split_workspace_bytes",
+    "divmod", "divmod_noalloc", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
     "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host", "host_sync",
     "add_chain", "poly", "poly_workspace_bytes",
@@ -41,6 +42,8 @@ SIGNATURES = {
     "bigint_sub": ([_P, _P, _P, _P, _I64, _I32, _P], ctypes.c_int),
     "bigint_mul": ([_P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "bigint_mul_lo": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P], ctypes.c_int),
+    "bigint_mul_split": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
+    "bigint_mul_split_workspace": ([_I64, _I32, _I32], _SZ),
     "bigint_divmod": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_divmod_workspace": ([_I64, _I32, _I32], _SZ),
     "bigint_divmod_noalloc": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
@@ -182,6 +185,29 @@ def mul(a, b, out=None, stream=None):
     rc = load().bigint_mul(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
                            _stream_ptr(stream))
     _check(rc, "bigint_mul")
+    return out
+
+
+def mul_split_workspace_bytes(count: int, na: int, nb: int) -> int:
+    return int(load().bigint_mul_split_workspace(count, na, nb))
+
+
+def mul_split(a, b, out=None, workspace=None, stream=None):
+    """Full product as ``mul``, each product's output tiles on different CTAs
+    (lower latency for few, large products)."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, na = a.shape
+    nb = b.shape[1]
+    if b.shape[0] != count:
+        raise ValueError("batch sizes differ")
+    out = _empty_like_limbs(a, count, na + nb) if out is None else _dev_tensor(out, "out")
+    need = mul_split_workspace_bytes(count, na, nb)
+    if workspace is None:
+        workspace = _workspace(need, a.device)
+    rc = load().bigint_mul_split(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
+                                 workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                 _stream_ptr(stream))
+    _check(rc, "bigint_mul_split")
     return out
 
 

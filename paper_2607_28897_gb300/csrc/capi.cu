@@ -12,6 +12,9 @@ int launch_addsub(bool sub, const uint64_t *a, const uint64_t *b, uint64_t *out,
 int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                int nb, int nout, cudaStream_t st);
 int mul_max_limbs();
+size_t mul_split_workspace(int64_t count, int na, int nb);
+int launch_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+                     int nb, void *ws, size_t bytes, cudaStream_t st);
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
@@ -111,6 +114,22 @@ int bigint_mul_lo(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
   if (count == 0) return BIGINT_OK;
   if (!a || !b || !out) return BIGINT_EINVAL;
   return launch_mul(a, b, out, count, na, nb, m, as_stream(stream));
+}
+
+size_t bigint_mul_split_workspace(int64_t count, int32_t na, int32_t nb) {
+  if (count < 0 || na < 1 || nb < 1) return 0;
+  return mul_split_workspace(count, na, nb);
+}
+
+int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                     int32_t na, int32_t nb, void *workspace, size_t workspace_bytes,
+                     void *stream) {
+  if (count < 0 || count > 0x7fffffff || na < 1 || nb < 1) return BIGINT_EINVAL;
+  if (na > mul_max_limbs() || nb > mul_max_limbs()) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!a || !b || !out) return BIGINT_EINVAL;
+  return launch_mul_split(a, b, out, count, na, nb, workspace, workspace_bytes,
+                          as_stream(stream));
 }
 
 size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv) {

@@ -486,10 +486,18 @@ __device__ void tc_release(TcCtx &c) {
 // while the tensor core's queue is full, so on its own warp that wait does
 // not hold up any drain or Hankel build.  Without IW thread 0 issues.
 //
+// Split mode (SPLIT, lo = 0): only tile `tile` (columns [NT tile, NT tile +
+// W)) is computed, with no carry in, and neither the bias nor x's top bit is
+// accounted for; its limbs [16 NT tile, + nl) get their internal carries and
+// tile_carry[0..1] = (high word of its last column sum, carry out).  The
+// tiles of one product can so run on different CTAs; tc_split_finish then
+// links them (Sec. VI's per-instance work spread over several SMs).
+//
 // Returns false (and sets c.aborted) if a wait hit its limit.
-template <int NT, int G, bool IW = false, bool XC = true>
+template <int NT, int G, bool IW = false, bool XC = true, bool SPLIT = false>
 __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, const uint64_t *y,
-                                           int ny, uint64_t *out, int nout, int lo) {
+                                           int ny, uint64_t *out, int nout, int lo, int tile = 0,
+                                           uint64_t *tile_carry = nullptr) {
   constexpr int DRAIN = 2 * NT;                // threads that drain and build
   constexpr int THREADS = DRAIN + (IW ? 32 : 0);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -522,6 +530,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
     if (W > need) W = need;
     W = (W + 15) & ~15;
     if (16 * (c0 + W) <= lo) continue;  // band: the whole tile lies below limb lo
+    if (SPLIT && c0 != NT * tile) continue;
     if (L0 < 0) {
       L0 = 16 * c0;
       if (lo > 0 && tid == 0) c.sh->carry_hi = 1ull << 32;  // + 2^32 B^L0
@@ -619,11 +628,18 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
       };
       auto store = [&](int j, uint64_t v) { o[j] = v; };
       const uint32_t cout = blk_addsub<false>(nl, cprev, load, store, c.scr);
-      if (tid == 0) { c.sh->carry_hi = His[nl - 1]; c.sh->carry = cout; }
+      if (tid == 0) {
+        c.sh->carry_hi = His[nl - 1];
+        c.sh->carry = cout;
+        if (SPLIT) {
+          tile_carry[0] = His[nl - 1];
+          tile_carry[1] = cout;
+        }
+      }
       __syncthreads();
     }
   }
-  if (L0 >= 0) {  // subtract the bias sum 2^31 sum_s 2^(8 s) over the computed tiles
+  if (!SPLIT && L0 >= 0) {  // subtract the bias sum 2^31 sum_s 2^(8 s) over the computed tiles
     uint64_t *o = out + L0;
     auto load = [&](int j) {
       return make_ulonglong2(o[j], j == 0 ? 0x8080808080000000ull : 0x8080808080808080ull);

@@ -43,6 +43,55 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
   tc_release<NT>(c);
 }
 
+// Split products: unit u is tile u % T of product u / T (tc_product's split
+// mode), its outgoing (high word, carry) at tile_carry[2 u], [2 u + 1].
+template <int NT, int G>
+__global__ void __launch_bounds__(2 * NT + 32, 1)
+    k_mul_tc_split(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
+                   uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count, int T,
+                   uint64_t *tile_carry) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ TcShared sh;
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  TcCtx c;
+  tc_init<NT>(c, sm, &sh, scr);
+  const int64_t units = count * T;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t inst = u / T;
+    if (!tc_product<NT, G, true, true, true>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny,
+                                             ny, Out + inst * (int64_t)nout, nout, 0,
+                                             (int)(u - inst * T), tile_carry + 2 * u))
+      break;
+  }
+  tc_release<NT>(c);
+}
+
+// One CTA per product: tile t (limbs [t L, t L + L), L = tile_limbs) was
+// computed without what flows in from tile t - 1, i.e. the high word H of
+// that tile's last column sum and its carry out k.  So the product is the
+// concatenated tiles plus sum_t (H_t + k_t) B^((t + 1) L), less the bias sum
+// of the column sums (as in the unsplit product): two carry passes.
+__global__ void __launch_bounds__(512)
+    k_tc_split_finish(uint64_t *Out, int nout, int T, int tile_limbs, const uint64_t *tile_carry) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  uint64_t *o = Out + (int64_t)blockIdx.x * nout;
+  const uint64_t *tc = tile_carry + 2 * (int64_t)blockIdx.x * T;
+  auto st = [&](int j, uint64_t v) { o[j] = v; };
+  auto ld_links = [&](int j) {
+    uint64_t v = 0;
+    if (j > 0 && j % tile_limbs == 0) {
+      const int t = j / tile_limbs - 1;
+      v = tc[2 * t] + tc[2 * t + 1];
+    }
+    return make_ulonglong2(o[j], v);
+  };
+  blk_addsub<false>(nout, 0u, ld_links, st, scr);
+  auto ld_bias = [&](int j) {
+    return make_ulonglong2(o[j], j == 0 ? 0x8080808080000000ull : 0x8080808080808080ull);
+  };
+  blk_addsub<true>(nout, 0u, ld_bias, st, scr);
+}
+
 }  // namespace tcm
 
 // ---------------------------------------------------------------------------
@@ -159,6 +208,97 @@ int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
       return tc_smem<256, 8, true>(nx, ny) ? launch_tc<256, 8, true>(x, y, out, count, nx, ny, nout, st)
                                            : launch_tc<256, 4, true>(x, y, out, count, nx, ny, nout, st);
   }
+}
+
+// ---- split products ----------------------------------------------------------
+int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na, int nb,
+               int nout, cudaStream_t st);
+
+namespace {
+
+constexpr int SPLIT_NT = 256, SPLIT_TILE_LIMBS = 16 * SPLIT_NT;
+
+template <int G>
+int split_dyn_max() {
+  static int dyn = -1;
+  if (dyn < 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc_split<SPLIT_NT, G>) != cudaSuccess) return 0;
+    const int d = optin - (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(tcm::k_mul_tc_split<SPLIT_NT, G>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d) != cudaSuccess)
+      return 0;
+    dyn = d;
+  }
+  return dyn;
+}
+
+template <int G>
+int launch_split(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_t count, int nx, int ny,
+                 int T, uint64_t *tile_carry, cudaStream_t st) {
+  const size_t smem = tcm::layout<SPLIT_NT, G>(nx, ny).total;
+  const int dyn = split_dyn_max<G>();
+  if (dyn <= 0 || smem > (size_t)dyn) return BIGINT_EINVAL;
+  int dev = 0, sms = 0;
+  BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+  BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t units = count * T, grid = units < sms ? units : sms;
+  const int nout = nx + ny;
+  tcm::k_mul_tc_split<SPLIT_NT, G><<<(unsigned)grid, 2 * SPLIT_NT + 32, smem, st>>>(
+      x, y, out, nx, ny, nout, count, T, tile_carry);
+  int rc = bigint_launch_status();
+  if (rc != BIGINT_OK) return rc;
+  tcm::k_tc_split_finish<<<(unsigned)count, 512, 0, st>>>(out, nout, T, SPLIT_TILE_LIMBS,
+                                                         tile_carry);
+  return bigint_launch_status();
+}
+
+// Shared memory a split CTA may take (the opt-in limit per block of sm_100
+// and sm_103, less room for the kernel's static shared memory).
+constexpr size_t SPLIT_SMEM_CAP = 232448 - 2048;
+
+// Tiles of an nx x ny split product, or 0 if it does not run split (not on
+// the 256-column tile with the carry digit, x too large for shared memory,
+// or a single tile).
+int split_tiles(int nx, int ny) {
+  if (nx < 1 || ny > 16383 || tc_shape(nx, ny) != TC_256) return 0;
+  if (tcm::layout<SPLIT_NT, 4>(nx, ny).total > SPLIT_SMEM_CAP) return 0;
+  const int T = (nx + ny + SPLIT_TILE_LIMBS - 1) / SPLIT_TILE_LIMBS;
+  return T >= 2 ? T : 0;
+}
+
+}  // namespace
+
+size_t mul_split_workspace(int64_t count, int na, int nb) {
+  const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
+  return (size_t)16 * (size_t)count * (size_t)split_tiles(nx, ny);
+}
+
+// The full products of launch_mul with each product's tiles on different
+// CTAs (split_tiles), or launch_mul itself where the product has one tile or
+// another shape.
+int launch_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
+                     int nb, void *ws, size_t bytes, cudaStream_t st) {
+  const uint64_t *x = a, *y = b;
+  int nx = na, ny = nb;
+  if (nb < na) { x = b; y = a; nx = nb; ny = na; }
+  const int T = split_tiles(nx, ny);
+  if (T == 0 || count == 0) return launch_mul(a, b, out, count, na, nb, na + nb, st);
+  if (bytes < mul_split_workspace(count, na, nb)) return BIGINT_ENOMEM;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % 8) != 0) return BIGINT_EINVAL;
+  uint64_t *tcarry = static_cast<uint64_t *>(ws);
+  const size_t s8 = tcm::layout<SPLIT_NT, 8>(nx, ny).total;
+  const size_t s4 = tcm::layout<SPLIT_NT, 4>(nx, ny).total;
+  if (split_dyn_max<8>() > 0 && s8 <= (size_t)split_dyn_max<8>())
+    return launch_split<8>(x, y, out, count, nx, ny, T, tcarry, st);
+  if (split_dyn_max<4>() > 0 && s4 <= (size_t)split_dyn_max<4>())
+    return launch_split<4>(x, y, out, count, nx, ny, T, tcarry, st);
+  return launch_mul(a, b, out, count, na, nb, na + nb, st);
 }
 
 // BIGINT_ETIMEOUT if a tensor-core product hit a wait limit since the last

@@ -21,7 +21,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, BATCH_PERSISTENT, OP_DIVMOD, OP_MUL, load, op_dtype, divmod as _divmod, mul as _mul
+from . import Batch, BATCH_PERSISTENT, OP_DIVMOD, OP_MUL, load, op_dtype, divmod as _divmod
+from . import mul_split as _mul_split
 from . import inputs
 
 
@@ -150,7 +151,8 @@ def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048
 
 def run_per_request(w: Workload, limit: int | None = None):
     """The plain form: one uniform-entry-point call per request, in arrival
-    order, on one stream; a request launches once it has arrived."""
+    order, on one stream; a request launches once it has arrived.  A product
+    with several output tiles spreads them over CTAs (bigint_mul_split)."""
     import torch
 
     n = len(w.ops) if limit is None else min(limit, len(w.ops))
@@ -167,7 +169,7 @@ def run_per_request(w: Workload, limit: int | None = None):
         a = w.pool[o["a"]:o["a"] + o["na"]].to("cuda", non_blocking=True).view(1, -1)
         b = w.pool[o["b"]:o["b"] + o["nb"]].to("cuda", non_blocking=True).view(1, -1)
         if o["op"] == OP_MUL:
-            r = _mul(a, b)
+            r = _mul_split(a, b)
             r.to("cpu", non_blocking=True)
         else:
             q, r, _ = _divmod(a, b)

@@ -102,3 +102,60 @@ def test_same_as_integer_variant(bi):
     finally:
         bi.set_variant(0, TC)
     assert np.array_equal(p12, p8)
+
+
+@pytest.mark.parametrize("na,nb,count", [(2048, 2049, 3), (4096, 4096, 2), (3000, 5000, 2),
+                                         (1, 8000, 2), (8192, 8192, 2), (10000, 10000, 1),
+                                         (9000, 10000, 1), (2100, 2100, 170)])
+def test_split(bi, orc, na, nb, count):
+    """Each product's 4096-limb output tiles on different CTAs, linked by the
+    finishing kernel: bit-identical to the oracle and to the one-CTA form
+    (ragged last tiles, a one-limb operand, more units than SMs)."""
+    from paper_2607_28897_gb300 import inputs
+
+    a = inputs.limbs(1200 + na, count, na)
+    b = inputs.limbs(1300 + nb, count, nb)
+    tiles = -(-(na + nb) // 4096)
+    assert bi.mul_split_workspace_bytes(count, na, nb) == 16 * count * tiles
+    da, db = to_dev(a), to_dev(b)
+    got = to_host(bi.mul_split(da, db))
+    assert np.array_equal(got, orc.batch_mul(a, b))
+    assert np.array_equal(got, to_host(bi.mul(da, db)))
+    bi.check_timeout()
+
+
+@pytest.mark.parametrize("pattern", [0xFFFFFFFFFFFFFFFF, 0x7F807F807F807F80,
+                                     0x8080808080808080, 0x0000000000000080])
+def test_split_extreme_digits(bi, orc, pattern):
+    """Digit patterns at the accumulator bound and all-ones operands, whose
+    products carry across the tile boundaries through long runs of ones."""
+    n = 8192
+    a = np.full((2, n), np.uint64(pattern), dtype=np.uint64)
+    b = a.copy()
+    b[1] = np.uint64(0xFFFFFFFFFFFFFFFF ^ pattern)
+    got = to_host(bi.mul_split(to_dev(a), to_dev(b)))
+    assert np.array_equal(got, orc.batch_mul(a, b))
+    bi.check_timeout()
+
+
+def test_split_small_shapes_run_unsplit(bi, orc):
+    """A product with one tile (or below the 256-column tile) needs no
+    workspace and runs as the ordinary product."""
+    from paper_2607_28897_gb300 import inputs
+
+    a = inputs.limbs(51, 4, 512)
+    b = inputs.limbs(52, 4, 512)
+    assert bi.mul_split_workspace_bytes(4, 512, 512) == 0
+    got = to_host(bi.mul_split(to_dev(a), to_dev(b)))
+    assert np.array_equal(got, orc.batch_mul(a, b))
+
+
+def test_split_workspace_too_small(bi):
+    import torch
+
+    from paper_2607_28897_gb300 import inputs
+
+    a = to_dev(inputs.limbs(53, 2, 4096))
+    ws = torch.empty(16 * 2 * 2 - 8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bi.BigIntError):
+        bi.mul_split(a, a, workspace=ws)
