@@ -80,6 +80,95 @@ __device__ uint32_t blk_addsub(int n, uint32_t cin, Load load, Store store, uint
 }
 
 // ---------------------------------------------------------------------------
+// r_j = (x_j + y_j + carry) - z_j - borrow, j in [0, n), in one pass over the
+// data: blk_addsub's carry scan for the sum, then the same scan as a borrow
+// chain for the difference on the sums held in registers.  `load(j)` gives
+// (x_j, y_j), `sub(j)` z_j.  *c / *b carry the carry / borrow in and out
+// (out of limb n - 1), so a long operand can be processed in pieces.
+// ---------------------------------------------------------------------------
+template <class Load, class Sub, class Store>
+__device__ void blk_add_then_sub(int n, uint32_t *c, uint32_t *b, Load load, Sub sub, Store store,
+                                 uint32_t *sm) {
+  constexpr int R = 4;
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  uint32_t *s_g = sm, *s_p = sm + 32;
+  uint32_t c_super = *c, b_super = *b;
+  // carry (borrow) into this warp's segment and out of the block from the
+  // per-warp (generate, propagate) of wc[]
+  auto resolve = [&](const WarpCarry (&wc)[R], uint32_t cin, uint32_t *cw, uint32_t *cout) {
+    uint32_t wg = 0, wp = 1;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      wg = warp_carry_out(wc[r], 0) | (warp_all_propagate(wc[r]) & wg);
+      wp &= warp_all_propagate(wc[r]);
+    }
+    if (lane == 0) { s_g[warp] = wg; s_p[warp] = wp; }
+    __syncthreads();
+    const uint32_t gw = (int)lane < nwarps ? s_g[lane] : 0;
+    const uint32_t pw = (int)lane < nwarps ? s_p[lane] : 1;
+    const uint64_t cm = warp_carries(warp_gp(gw, pw), cin);
+    *cw = (uint32_t)(cm >> warp) & 1u;
+    *cout = (uint32_t)(cm >> nwarps) & 1u;
+    __syncthreads();  // s_g, s_p are reused
+  };
+  for (int base = 0; base < n; base += nwarps * R * 32) {
+    const int wb = base + warp * R * 32;
+    uint64_t s[R];
+    WarpCarry wc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int j = wb + r * 32 + (int)lane;
+      uint32_t g = 0, p = 1;
+      s[r] = 0;
+      if (j < n) {
+        const ulonglong2 xy = load(j);
+        const uint64_t t = xy.x + xy.y;
+        g = t < xy.x;
+        p = t == ~0ull;
+        s[r] = t;
+      }
+      wc[r] = warp_gp(g, p);
+    }
+    uint32_t cw, cout;
+    resolve(wc, c_super, &cw, &cout);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint64_t lc = warp_carries(wc[r], cw);
+      s[r] += (lc >> lane) & 1u;
+      cw = (uint32_t)(lc >> 32) & 1u;
+    }
+    c_super = cout;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int j = wb + r * 32 + (int)lane;
+      uint32_t g = 0, p = 1;
+      if (j < n) {
+        const uint64_t z = sub(j), t = s[r] - z;
+        g = s[r] < z;
+        p = t == 0;
+        s[r] = t;
+      }
+      wc[r] = warp_gp(g, p);
+    }
+    uint32_t bw, bout;
+    resolve(wc, b_super, &bw, &bout);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint64_t lb = warp_carries(wc[r], bw);
+      const uint32_t bl = (uint32_t)(lb >> lane) & 1u;
+      bw = (uint32_t)(lb >> 32) & 1u;
+      const int j = wb + r * 32 + (int)lane;
+      if (j < n) store(j, s[r] - bl);
+    }
+    b_super = bout;
+  }
+  *c = c_super;
+  *b = b_super;
+}
+
+// ---------------------------------------------------------------------------
 // Block-wide maximum of one int per thread (all threads get the result).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int blk_max(int v, uint32_t *sm) {

@@ -412,6 +412,7 @@ struct TcShared {
   uint64_t bars[2];   // mbarriers: MMAs of the group in accumulator b completed
   uint64_t carry_hi;  // high word carried into the next tile's first limb
   uint32_t carry;     // carry bit carried into the next tile
+  uint32_t borrow;    // borrow of the bias subtraction carried into the next tile
   uint32_t tmem_slot;
 };
 
@@ -518,7 +519,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   for (int i = tid; i < ZB * 128 / 16; i += THREADS)
     reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
   fill_x<XC>(sm + Ly.xs, x, nx, Ly.ptot);
-  if (tid == 0) { c.sh->carry_hi = 0; c.sh->carry = 0; }
+  if (tid == 0) { c.sh->carry_hi = 0; c.sh->carry = 0; c.sh->borrow = 0; }
   fence_async_smem();
   __syncthreads();
 
@@ -627,25 +628,32 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
         return make_ulonglong2(o[j], j == 0 ? hprev : (uint64_t)His[j - 1]);
       };
       auto store = [&](int j, uint64_t v) { o[j] = v; };
-      const uint32_t cout = blk_addsub<false>(nl, cprev, load, store, c.scr);
-      if (tid == 0) {
-        c.sh->carry_hi = His[nl - 1];
-        c.sh->carry = cout;
-        if (SPLIT) {
+      if (SPLIT) {
+        const uint32_t cout = blk_addsub<false>(nl, cprev, load, store, c.scr);
+        if (tid == 0) {
           tile_carry[0] = His[nl - 1];
           tile_carry[1] = cout;
+        }
+      } else {
+        // with the bias sum 2^31 sum_s 2^(8 s) of the column sums subtracted
+        // in the same pass (0x8080808080808080 per limb from L0 on,
+        // 0x8080808080000000 in limb L0); the carry and the borrow run on
+        // into the next tile
+        uint32_t cc = cprev, bb = c.sh->borrow;
+        auto bias = [&](int j) {
+          return j0 + j == L0 ? 0x8080808080000000ull : 0x8080808080808080ull;
+        };
+        blk_add_then_sub(nl, &cc, &bb, load, bias, store, c.scr);
+        if (tid == 0) {
+          c.sh->carry_hi = His[nl - 1];
+          c.sh->carry = cc;
+          c.sh->borrow = bb;
         }
       }
       __syncthreads();
     }
   }
-  if (!SPLIT && L0 >= 0) {  // subtract the bias sum 2^31 sum_s 2^(8 s) over the computed tiles
-    uint64_t *o = out + L0;
-    auto load = [&](int j) {
-      return make_ulonglong2(o[j], j == 0 ? 0x8080808080000000ull : 0x8080808080808080ull);
-    };
-    auto store = [&](int j, uint64_t v) { o[j] = v; };
-    blk_addsub<true>(nout - L0, 0u, load, store, c.scr);
+  if (!SPLIT && L0 >= 0) {
     // without x's carry digit the digits spelled x_s = x - t_x B^nx:
     // x y = x_s y + t_x y B^nx.  In band mode the part of the correction
     // below L0 is dropped (its carry into L0 is within the band's margin).
