@@ -324,7 +324,7 @@ int bigint_host_sync(void);
  *   limbs; otherwise variant 8).  One persistent CTA per SM, which holds
  *   all of the SM's tensor memory while it runs.
  * op 1 = division (divmod and shinv):
- *   variant 0 (default) or 1: operands of 2048 limbs and more run in a
+ *   variant 0 (default) or 1: operands of 1536 limbs and more run in a
  *   kernel that holds its SM's tensor memory and computes products whose
  *   shorter operand has at least 256 limbs on the tensor cores (as variant
  *   12 of the multiply); smaller divisions use the integer products

@@ -43,7 +43,8 @@ def check(bi, orc, u, v):
 
 @pytest.mark.parametrize("nu,nv", [(2048, 1024), (2048, 256), (2048, 300), (2048, 1800),
                                    (2048, 2048), (3000, 1500), (4096, 2), (4096, 700),
-                                   (5000, 4999), (2100, 7), (6000, 2500)])
+                                   (5000, 4999), (2100, 7), (6000, 2500), (1536, 768),
+                                   (1536, 1), (1600, 800), (1535, 700)])
 def test_shapes(bi, orc, nu, nv):
     from paper_2607_28897_gb300 import inputs
 
@@ -94,7 +95,7 @@ def test_quotient_near_power(bi, orc):
     check(bi, orc, np.stack(rows_u), np.stack(rows_v))
 
 
-@pytest.mark.parametrize("n,count", [(2048, 48), (8192, 6)])
+@pytest.mark.parametrize("n,count", [(768, 64), (2048, 48), (8192, 6)])
 def test_same_as_integer_products(bi, n, count):
     from paper_2607_28897_gb300 import inputs
 
@@ -111,7 +112,8 @@ def test_same_as_integer_products(bi, n, count):
     assert np.array_equal(s0.cpu().numpy(), s2.cpu().numpy())
 
 
-@pytest.mark.parametrize("nv,h", [(2048, 4096), (1500, 2100), (300, 5000), (4096, 4096)])
+@pytest.mark.parametrize("nv,h", [(2048, 4096), (1500, 2100), (300, 5000), (4096, 4096),
+                                  (768, 1536)])
 def test_shinv(bi, orc, nv, h):
     from paper_2607_28897_gb300 import inputs
 
