@@ -164,6 +164,24 @@ int bigint_shinv(const uint64_t *v, uint64_t *w, int32_t *status,
                  void *workspace, size_t workspace_bytes, void *stream);
 size_t bigint_shinv_workspace(int64_t count, int32_t nv, int32_t h);
 
+/* Division by a shifted inverse computed once and reused (Sec. V-C: the
+ * quotient is floor(u w / B^h) up to the exact final correction; here w is
+ * an input, e.g. from bigint_shinv, so many dividends share one divisor's
+ * Newton loop).  w = floor(B^h / v) exactly, nw limbs, h >= nu, h >= nv,
+ * nw <= h + 1; the kernel takes the top limbs of w, floor(w / B^(h - k)) =
+ * floor(B^k / v) with k = prec(u), and finishes as bigint_divmod does.
+ * v_stride: nv (one divisor per instance) or 0 (one divisor for the whole
+ * batch, v holds nv limbs); w_stride likewise nw or 0.  q, r, status and
+ * the workspace (bigint_divmod_workspace(count, nu, nv) bytes) as for
+ * bigint_divmod.  w is not checked: a value other than that inverse gives
+ * BIGINT_EINTERNAL where the correction does not settle (a w far off), and
+ * otherwise no guarantee on q and r.                                       */
+int bigint_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w,
+                      uint64_t *q, uint64_t *r, int32_t *status, int64_t count,
+                      int32_t nu, int32_t nv, int32_t nw, int32_t h,
+                      int64_t v_stride, int64_t w_stride, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
 /* ---- ragged batches of mixed operations (the batched form) --------------
  * A batch is an array of operation descriptors over one input pool and one
  * output pool of limbs (device memory, caller-owned).  Offsets are in limbs

@@ -16,7 +16,7 @@ import os
 
 __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "mul_split", "mul_split_workspace_bytes",
-    "divmod", "divmod_noalloc", "shinv",
+    "divmod", "divmod_noalloc", "divmod_inv", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
     "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host", "host_sync",
     "add_chain", "poly", "poly_workspace_bytes",
@@ -50,6 +50,8 @@ SIGNATURES = {
     "bigint_divmod_noalloc_scratch_bytes": ([], _SZ),
     "bigint_shinv": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_shinv_workspace": ([_I64, _I32, _I32], _SZ),
+    "bigint_divmod_inv": ([_P, _P, _P, _P, _P, _P, _I64, _I32, _I32, _I32, _I32, _I64, _I64, _P,
+                           _SZ, _P], ctypes.c_int),
     "bigint_batch_create": ([_P, _I64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "bigint_batch_workspace": ([_P], _SZ),
     "bigint_batch_upload": ([_P, _P, _SZ, _P], ctypes.c_int),
@@ -275,6 +277,36 @@ def divmod_noalloc(u, v, q=None, r=None, status=None, stream=None):
     rc = load().bigint_divmod_noalloc(u.data_ptr(), v.data_ptr(), q.data_ptr(), r.data_ptr(),
                                       status.data_ptr(), count, nu, nv, _stream_ptr(stream))
     _check(rc, "bigint_divmod_noalloc")
+    return q, r, status
+
+
+def divmod_inv(u, v, w, h: int, q=None, r=None, status=None, workspace=None, stream=None):
+    """q, r and status as ``divmod``, from w = floor(B^h / v) (``shinv``),
+    h >= nu.  v (nv limbs) and w (nw limbs) are (count, n) tensors, one per
+    instance, or (1, n): one divisor and inverse for the whole batch."""
+    torch = _torch()
+    u, v, w = _dev_tensor(u, "u"), _dev_tensor(v, "v"), _dev_tensor(w, "w")
+    count, nu = u.shape
+    nv, nw = v.shape[1], w.shape[1]
+    for t, name in ((v, "v"), (w, "w")):
+        if t.shape[0] not in (1, count):
+            raise ValueError(f"{name} must have 1 or {count} rows")
+    vs = 0 if (v.shape[0] == 1 and count != 1) else nv
+    ws_ = 0 if (w.shape[0] == 1 and count != 1) else nw
+    nq = max(nu - nv + 1, 1)
+    q = _empty_like_limbs(u, count, nq) if q is None else _dev_tensor(q, "q")
+    r = _empty_like_limbs(u, count, nv) if r is None else _dev_tensor(r, "r")
+    if status is None:
+        status = torch.empty(count, dtype=torch.int32, device=u.device)
+    need = divmod_workspace_bytes(count, nu, nv)
+    if workspace is None:
+        workspace = _workspace(need, u.device)
+    rc = load().bigint_divmod_inv(u.data_ptr(), v.data_ptr(), w.data_ptr(), q.data_ptr(),
+                                  r.data_ptr(), status.data_ptr(), count, nu, nv, nw, h, vs, ws_,
+                                  workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(),
+                                  _stream_ptr(stream))
+    _check(rc, "bigint_divmod_inv")
     return q, r, status
 
 

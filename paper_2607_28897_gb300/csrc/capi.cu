@@ -39,6 +39,9 @@ size_t divmod_workspace(int64_t count, int nu, int nv);
 int launch_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count, int nv,
                  int h, int nw, void *ws, size_t ws_bytes, cudaStream_t st);
 size_t shinv_workspace(int64_t count, int nv, int h);
+int launch_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w, uint64_t *q,
+                      uint64_t *r, int32_t *status, int64_t count, int nu, int nv, int nw, int h,
+                      int64_t v_stride, int64_t w_stride, void *ws, cudaStream_t st);
 int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out);
 size_t batch_workspace_bytes(const bigint_batch *B);
 int batch_upload(bigint_batch *B, void *ws, size_t bytes, cudaStream_t st);
@@ -130,6 +133,24 @@ int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_
   if (!a || !b || !out) return BIGINT_EINVAL;
   return launch_mul_split(a, b, out, count, na, nb, workspace, workspace_bytes,
                           as_stream(stream));
+}
+
+int bigint_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w, uint64_t *q,
+                      uint64_t *r, int32_t *status, int64_t count, int32_t nu, int32_t nv,
+                      int32_t nw, int32_t h, int64_t v_stride, int64_t w_stride,
+                      void *workspace, size_t workspace_bytes, void *stream) {
+  if (count < 0 || count > 0x7fffffff || nu < 1 || nv < 1 || nw < 1) return BIGINT_EINVAL;
+  if (nu > BIGINT_MAX_LIMBS || nv > BIGINT_MAX_LIMBS) return BIGINT_EINVAL;
+  if (h < nu || h < nv || h > 2 * BIGINT_MAX_LIMBS || nw > h + 1) return BIGINT_EINVAL;
+  if (v_stride != 0 && v_stride != nv) return BIGINT_EINVAL;
+  if (w_stride != 0 && w_stride != nw) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!u || !v || !w || !q || !r) return BIGINT_EINVAL;
+  if (workspace_bytes < divmod_workspace(count, nu, nv)) return BIGINT_ENOMEM;
+  if (workspace_bytes > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0))
+    return BIGINT_EINVAL;
+  return launch_divmod_inv(u, v, w, q, r, status, count, nu, nv, nw, h, v_stride, w_stride,
+                           workspace, as_stream(stream));
 }
 
 size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv) {

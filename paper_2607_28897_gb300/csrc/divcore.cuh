@@ -355,43 +355,21 @@ __device__ int correct(const uint64_t *v, int kv, uint64_t *R, uint64_t *Qh, int
 }
 
 
-// One division q = floor(u / v), r = u - q v by the whole CTA (Sec. V-C):
-// the shifted inverse by Newton steps, q^ = floor(u w / B^h), r^ computed
-// modulo B^(k+2), exact correction.  ws: this instance's workspace region of
-// ws_limbs(nu, nv, nu) limbs.  Returns the status (0, EDIVZERO, ERANGE,
-// EINTERNAL).
-template <int RB, int Q, int F, bool TC = false>
-__device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q,
-                          int nq, uint64_t *r, uint64_t *ws, uint32_t *smem, int smem_words,
-                          uint32_t *scr, tcm::TcCtx *tc = nullptr) {
-  Work W = carve(ws, nu, nv, nu);
+// q = floor(u / v), r = u - q v from the inverse w = floor(B^h / v) (nw
+// limbs) at h = ku = prec(u) >= kv = prec(v): q^ = floor(u w / B^h), from a
+// product that may drop the columns below limb h - 2, is at most a few units
+// low (integer product: it is never high, since w <= B^h / v) or one unit
+// high (tensor-core product, whose band mode adds a margin above the dropped
+// columns); the final correction absorbs either.  u w + B^h < B^(ku + nw)
+// since h = ku, so the banded value never wraps.
+template <int RB, int Q, int F, bool TC>
+__device__ int divmod_tail(const uint64_t *u, int ku, const uint64_t *v, int kv,
+                           const uint64_t *w, int nw, int h, uint64_t *q, int nq, uint64_t *r,
+                           int nv, Work &W, uint32_t *smem, int smem_words, uint32_t *scr,
+                           tcm::TcCtx *tc) {
   int st = BIGINT_OK;
-  const int kv = blk_prec(v, nv, scr);
-  if (kv == 0) {  // division by zero: q = r = 0
-    blk_zero(q, nq);
-    blk_zero(r, nv);
-    __syncthreads();
-    return BIGINT_EDIVZERO;
-  }
-  const int k = kv - 1;
-  const int ku = blk_prec(u, nu, scr);
-  if (ku < kv) {  // u < B^(ku) <= B^(kv-1) <= v: q = 0, r = u
-    blk_zero(q, nq);
-    for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = j < ku ? u[j] : 0;
-    __syncthreads();
-    return BIGINT_OK;
-  }
-  const int h = ku;
-  int nw = shinv_newton<RB, Q, F, TC>(v, k, h, W, smem, smem_words, scr, tc);
-  // q^ = floor(u w / B^h), from a product that may drop the columns below
-  // limb h - 2: q^ is then at most a few units low (integer product: it is
-  // never high, since w <= B^h / v) or one unit high (tensor-core product,
-  // whose band mode adds a margin above the dropped columns); the final
-  // correction absorbs either.  u w + B^h < B^(ku + nw) since h = ku, so
-  // the banded value never wraps.
   const int nz = ku + nw;
-  mul_any<RB, Q, F, TC>(u, ku, W.w, nw, W.p, nz, W.tmp, smem, smem_words, h > 2 ? h - 2 : 0,
-                        tc);
+  mul_any<RB, Q, F, TC>(u, ku, w, nw, W.p, nz, W.tmp, smem, smem_words, h > 2 ? h - 2 : 0, tc);
   const int nqh = nz - h > 0 ? nz - h : 0;
   const int qcap = nqh + 1 < W.cap_w ? nqh + 1 : W.cap_w;
   for (int j = threadIdx.x; j < qcap; j += blockDim.x) W.qh[j] = j < nqh ? W.p[h + j] : 0;
@@ -419,6 +397,38 @@ __device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, 
   __syncthreads();
   return st;
 }
+
+// One division q = floor(u / v), r = u - q v by the whole CTA (Sec. V-C):
+// the shifted inverse by Newton steps, q^ = floor(u w / B^h), r^ computed
+// modulo B^(k+2), exact correction.  ws: this instance's workspace region of
+// ws_limbs(nu, nv, nu) limbs.  Returns the status (0, EDIVZERO, ERANGE,
+// EINTERNAL).
+template <int RB, int Q, int F, bool TC = false>
+__device__ int divmod_one(const uint64_t *u, int nu, const uint64_t *v, int nv, uint64_t *q,
+                          int nq, uint64_t *r, uint64_t *ws, uint32_t *smem, int smem_words,
+                          uint32_t *scr, tcm::TcCtx *tc = nullptr) {
+  Work W = carve(ws, nu, nv, nu);
+  const int kv = blk_prec(v, nv, scr);
+  if (kv == 0) {  // division by zero: q = r = 0
+    blk_zero(q, nq);
+    blk_zero(r, nv);
+    __syncthreads();
+    return BIGINT_EDIVZERO;
+  }
+  const int k = kv - 1;
+  const int ku = blk_prec(u, nu, scr);
+  if (ku < kv) {  // u < B^(ku) <= B^(kv-1) <= v: q = 0, r = u
+    blk_zero(q, nq);
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = j < ku ? u[j] : 0;
+    __syncthreads();
+    return BIGINT_OK;
+  }
+  const int h = ku;
+  int nw = shinv_newton<RB, Q, F, TC>(v, k, h, W, smem, smem_words, scr, tc);
+  return divmod_tail<RB, Q, F, TC>(u, ku, v, kv, W.w, nw, h, q, nq, r, nv, W, smem, smem_words,
+                                   scr, tc);
+}
+
 
 }  // namespace
 }  // namespace divc

@@ -34,7 +34,13 @@ namespace bigint {
 using namespace divc;
 
 
-// mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw).
+// mode 0: divmod (q, r); mode 1: shinv (w = floor(B^h / v) into q, nq = nw);
+// mode 2: divmod (q, r) from a given inverse Wg = floor(B^h / v) (nwg limbs,
+// h >= nu): floor(floor(B^h / v) / B^s) = floor(B^(h-s) / v), so the top
+// limbs of Wg are the inverse at h - s = prec(u), the one mode 0 computes,
+// and the division finishes as mode 0 does without the Newton steps.
+// v_stride / w_stride: limbs between the instances' divisors / inverses (0:
+// one for the whole batch).
 // Thread cap per product variant: 512 gives the wide-chunk variant 128
 // registers (no spills in its products); the small variant keeps a 640 cap,
 // whose 96-register budget fits two blocks of ~320 threads on one SM.  The
@@ -50,14 +56,15 @@ template <int RB, int Q, int F, bool TC>
 __global__ void __launch_bounds__(div_max_threads<Q, TC>())
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,
              uint64_t *Ro, int32_t *status, int nu, int nv, int nq, int mode, int h_arg,
-             uint64_t *ws, int64_t ws_stride, int smem_words) {
+             uint64_t *ws, int64_t ws_stride, int smem_words, const uint64_t *Wg, int nwg,
+             int64_t v_stride, int64_t w_stride) {
   extern __shared__ __align__(1024) uint32_t smem[];
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   __shared__ tcm::TcShared tsh;
   const int64_t inst = blockIdx.x;
-  const uint64_t *v = V + inst * (int64_t)nv;
+  const uint64_t *v = V + inst * v_stride;
   uint64_t *q = Qo + inst * (int64_t)nq;
-  const int hcap = mode == 0 ? nu : h_arg;
+  const int hcap = mode == 1 ? h_arg : nu;
   Work W = carve(ws + inst * ws_stride, nu, nv, hcap);
   int st = BIGINT_OK;
   tcm::TcCtx tcc;
@@ -96,6 +103,32 @@ __global__ void __launch_bounds__(div_max_threads<Q, TC>())
       const int pw = blk_prec(W.w, W.cap_w, scr);
       if (pw > nq && st == BIGINT_OK) st = BIGINT_ERANGE;
       for (int j = threadIdx.x; j < nq; j += blockDim.x) q[j] = j < W.cap_w ? W.w[j] : 0;
+      return;
+    }
+
+    if (mode == 2) {
+      // ---- division from the given inverse
+      const uint64_t *u = U + inst * (int64_t)nu;
+      uint64_t *r = Ro + inst * (int64_t)nv;
+      const int ku = blk_prec(u, nu, scr);
+      if (ku < kv) {  // u < v: q = 0, r = u
+        blk_zero(q, nq);
+        for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = j < ku ? u[j] : 0;
+        __syncthreads();
+        return;
+      }
+      const uint64_t *wg = Wg + inst * w_stride;
+      const int s = h_arg - ku;  // inverse at h = ku: drop the low s limbs
+      const int pw = blk_prec(wg, nwg, scr);
+      const int nw = pw > s ? pw - s : 0;
+      if (nw == 0) {  // floor(B^ku / v) >= 1 for a true inverse: this w is not one
+        blk_zero(q, nq);
+        blk_zero(r, nv);
+        st = BIGINT_EINTERNAL;
+        return;
+      }
+      st = divmod_tail<RB, Q, F, TC>(u, ku, v, kv, wg + s, nw, ku, q, nq, r, nv, W, smem,
+                                     smem_words, scr, tc);
       return;
     }
 
@@ -155,10 +188,19 @@ size_t shinv_workspace(int64_t count, int nv, int h) {
   return (size_t)count * (size_t)ws_limbs(nv, nv, h) * sizeof(uint64_t);
 }
 
+// Operands of one launch beyond those of divmod: the given inverses of
+// mode 2 and the distance between the instances' divisors and inverses.
+struct DivExtra {
+  const uint64_t *w = nullptr;
+  int nw = 0;
+  int64_t v_stride = -1;  // -1: nv
+  int64_t w_stride = 0;
+};
+
 template <int RB, int Q, int F, bool TC>
 static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                               int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
-                              int h, void *ws, cudaStream_t st) {
+                              int h, void *ws, cudaStream_t st, const DivExtra &x) {
   const int optin = div_smem_optin();
   if (optin == 0) return BIGINT_ECUDA;
   static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
@@ -172,7 +214,7 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
   int smem_words = dyn_max / 4;
   // the largest product a division performs is about (2 H) x H limbs;
   // ask for no more shared memory than one such product needs
-  const int H = (mode == 0 ? nu : h);
+  const int H = (mode == 1 ? h : nu);
   int need = blk_mul_smem_words<RB, Q>(H, H);
   if (TC) {  // tensor-core products: shorter operand up to max(H - nv, nv) + a few limbs
     const int ns = (H - nv > nv ? H - nv : nv) + 8;
@@ -195,26 +237,26 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
     if (T < 64) T = 64;
     if (T > TMAX) T = TMAX;
   }
-  const int hcap = mode == 0 ? nu : h;
+  const int hcap = mode == 1 ? h : nu;
   const int64_t stride = ws_limbs(nu, nv, hcap);
   k_divmod<RB, Q, F, TC><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
       u, v, q, r, status, nu, nv, nq, mode, h, reinterpret_cast<uint64_t *>(ws), stride,
-      smem_words);
+      smem_words, x.w, x.nw, x.v_stride < 0 ? nv : x.v_stride, x.w_stride);
   return bigint_launch_status();
 }
 
 static int launch_div_common(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                              int32_t *status, int64_t count, int nu, int nv, int nq, int mode,
-                             int h, void *ws, cudaStream_t st) {
-  const int H = (mode == 0 ? nu : h);
+                             int h, void *ws, cudaStream_t st, const DivExtra &x = DivExtra()) {
+  const int H = (mode == 1 ? h : nu);
   if (H < DIV_SMALL_LIMBS)
     return launch_div_variant<SRB, SQ, SF, false>(u, v, q, r, status, count, nu, nv, nq, mode, h,
-                                                  ws, st);
+                                                  ws, st, x);
   if (g_div_tc)
     return launch_div_variant<DRB, DQ, DF, true>(u, v, q, r, status, count, nu, nv, nq, mode, h,
-                                                 ws, st);
+                                                 ws, st, x);
   return launch_div_variant<DRB, DQ, DF, false>(u, v, q, r, status, count, nu, nv, nq, mode, h,
-                                                ws, st);
+                                                ws, st, x);
 }
 
 int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
@@ -222,6 +264,20 @@ int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r
                   cudaStream_t st) {
   const int nq = nu - nv + 1 > 1 ? nu - nv + 1 : 1;
   return launch_div_common(u, v, q, r, status, count, nu, nv, nq, 0, nu, ws, st);
+}
+
+// q, r of u / v from w = floor(B^h / v) (h >= nu, h >= nv), per instance or
+// shared (strides 0); the workspace of launch_divmod.
+int launch_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w, uint64_t *q,
+                      uint64_t *r, int32_t *status, int64_t count, int nu, int nv, int nw, int h,
+                      int64_t v_stride, int64_t w_stride, void *ws, cudaStream_t st) {
+  const int nq = nu - nv + 1 > 1 ? nu - nv + 1 : 1;
+  DivExtra x;
+  x.w = w;
+  x.nw = nw;
+  x.v_stride = v_stride;
+  x.w_stride = w_stride;
+  return launch_div_common(u, v, q, r, status, count, nu, nv, nq, 2, h, ws, st, x);
 }
 
 int launch_shinv(const uint64_t *v, uint64_t *w, int32_t *status, int64_t count, int nv, int h,

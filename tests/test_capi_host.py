@@ -45,6 +45,32 @@ def test_mul_split_checks(L):
                               None) == bi.EINVAL
 
 
+def test_divmod_inv_checks(L):
+    """Division by a given inverse: h must cover both operands, w at most
+    h + 1 limbs, strides nv / nw or 0, and the divmod workspace."""
+    import paper_2607_28897_gb300 as bi
+
+    p = ctypes.c_void_p(256)
+    need = L.bigint_divmod_workspace(8, 64, 32)
+    args = dict(u=p, v=p, w=p, q=p, r=p, st=None, count=8, nu=64, nv=32, nw=34, h=64, vs=32,
+                wst=34, ws=p, nb=need)
+
+    def call(**kw):
+        a = dict(args, **kw)
+        return L.bigint_divmod_inv(a["u"], a["v"], a["w"], a["q"], a["r"], a["st"], a["count"],
+                                   a["nu"], a["nv"], a["nw"], a["h"], a["vs"], a["wst"], a["ws"],
+                                   a["nb"], None)
+
+    assert call(h=63) == bi.EINVAL            # h < nu
+    assert call(nw=66) == bi.EINVAL           # nw > h + 1
+    assert call(vs=5) == bi.EINVAL            # stride neither nv nor 0
+    assert call(wst=7) == bi.EINVAL
+    assert call(count=-1) == bi.EINVAL
+    assert call(nb=need - 1) == bi.ENOMEM
+    assert call(ws=ctypes.c_void_p(264)) == bi.EINVAL
+    assert call(count=0, u=None, v=None, w=None, q=None, r=None) == bi.OK
+
+
 def test_divmod_workspace_checks(L):
     import paper_2607_28897_gb300 as bi
 
