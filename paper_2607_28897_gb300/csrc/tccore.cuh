@@ -46,24 +46,29 @@
 //    n <= 16383 limbs.
 //  * Output.  Each limb j is V_j = sum_k (coef(8j+k) + 2^31) 2^(8k) (biased
 //    so that all terms are unsigned): the limb's low 64 bits plus a high word
-//    that goes to limb j + 1 in one carry scan per tile (blk_addsub, the
-//    carry scan of Fig. 3), and the bias sum 2^31 sum_s 2^(8s) -- the word
-//    0x8080808080808080 in every limb, 0x8080808080000000 in limb 0 -- is
-//    subtracted at the end with one more borrow scan.
+//    that goes to limb j + 1, and the bias sum 2^31 sum_s 2^(8s) -- the word
+//    0x8080808080808080 in every limb, 0x8080808080000000 in limb 0 -- to
+//    subtract; both in one pass per tile (blk_add_then_sub: the carry scan
+//    of Fig. 3 for the sum, then as a borrow chain for the difference).
 //
-// Schedule: a persistent CTA of 2 NT threads loops over instances; per
-// instance over tiles of NT output columns; per tile over groups of G = 8
-// Toeplitz blocks (G = 4 when the longer Hankel buffers do not fit).  Fewer,
-// larger groups matter: every drain reads the whole accumulator out of
-// tensor memory, and the drains do not fully overlap the MMAs.  Thread 0 issues a group's MMAs into one of two NT-column
-// fp32 accumulators in tensor memory and commits them to an mbarrier; while
-// they run, all threads build the next group's Hankel core matrices (double
-// buffered) and drain the other accumulator.  NT = 256 (one CTA per SM, all
-// of its tensor memory) serves large products; NT = 128 (two CTAs per SM,
-// half the tensor memory each) keeps more work in flight for small ones.
-// Every wait has a cycle limit;
-// a CTA that reaches it stops, records the event for bigint_check_timeout()
-// and releases its tensor memory.
+// Schedule: a persistent CTA of 2 NT drain threads and one issuer warp loops
+// over instances; per instance over tiles of NT output columns; per tile
+// over groups of G Toeplitz blocks (8; 7 for NT = 64; 4 when the longer
+// Hankel buffers do not fit).  Fewer, larger groups matter: every drain
+// reads the whole accumulator out of tensor memory.  The issuer warp's lane
+// 0 issues a group's MMAs into one of two NT-column fp32 accumulators in
+// tensor memory and commits them to an mbarrier (it blocks on the tensor
+// core's shallow instruction queue for most of a group, hence a warp of its
+// own); meanwhile the drain threads drain the other accumulator and build
+// the next group's Hankel core matrices (double buffered; each y digit of
+// the group recoded once into a staging run, the rows copied out of it).
+// NT = 256 (one CTA per SM, all of its tensor memory) serves large
+// products; NT = 128 (two CTAs per SM) and NT = 64 (three) keep several
+// issuers per SM for small ones, where an MMA's time is its A operand's
+// shared-memory read rather than N.  Split mode computes one tile of a
+// product per call, so that a product's tiles can run on different CTAs.
+// Every wait has a cycle limit; a CTA that reaches it stops, records the
+// event for bigint_check_timeout() and releases its tensor memory.
 #pragma once
 #include <cuda_fp16.h>
 
@@ -91,8 +96,11 @@ struct Layout {
   int mx;    // x blocks of 128 digits (8 nx digits, + the carry digit if XC)
   int ey;    // last Toeplitz block index of y (e in [0, ey])
   int ctot;  // output columns with nonzero coefficients: mx + ey
-  int ptot;  // stored x blocks (16 zero blocks on each side)
-  uint32_t xs, z, h0, h1, cs, his, total;  // byte offsets in dynamic shared memory
+  int ptot;  // stored x blocks (16 zero blocks on each side; odd)
+  // byte offsets in dynamic shared memory: x (B layout), zero core matrices,
+  // the two Hankel buffers, the column-sum transpose area (also the Hankel
+  // staging run while a tile's groups run), high words of the tile's limbs
+  uint32_t xs, z, h0, h1, cs, his, total;
 };
 
 template <int NT, int G, bool XC = true>
