@@ -192,9 +192,14 @@ def cpu_model() -> str:
 # --------------------------------------------------------------------------
 def kernel_source_hash(files=("tccore.cuh", "tcmul.cu", "mul.cu", "blockops.cuh",
                               "common.cuh")) -> str:
+    """Hash of the multiply kernel's code: // comments, blank lines and
+    indentation do not count, so a comment edit keeps a profile valid."""
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, "paper_2607_28897_gb300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_2607_28897_gb300", "csrc", f)):
+            code = line.split("//", 1)[0].strip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
