@@ -585,17 +585,20 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
 
     def step():
         # every call is enqueued (sync=False): the copies of one call overlap
-        # the kernels of the next; one host_sync ends the step
-        for n in sizes:
+        # the kernels of the next; one host_sync ends the step.  Longest
+        # kernels first: while the 2^19-bit products run, the copies of the
+        # copy-bound additions behind them stream in (in the opposite order
+        # the additions' copies, 4.8 ms each, wait with an idle GPU)
+        for n in sorted(sizes, reverse=True):
             ha, hb, hsa, hsb = host_in[n]
             hs, hd, hp, hc, hbw = host_out[n]
             w = ws[n]
+            timed(f"mul_{n}", lambda: bi.mul_host(ha, hb, out=hp, workspace=w[bi.OP_MUL],
+                                                  sync=False))
             timed(f"add_{n}", lambda: bi.add_host(ha, hb, out=hs, carry=hc,
                                                   workspace=w[bi.OP_ADD], sync=False))
             timed(f"sub_{n}", lambda: bi.sub_host(hsa, hsb, out=hd, borrow=hbw,
                                                   workspace=w[bi.OP_SUB], sync=False))
-            timed(f"mul_{n}", lambda: bi.mul_host(ha, hb, out=hp, workspace=w[bi.OP_MUL],
-                                                  sync=False))
         for n, _ in DIV:
             hu, hv, hq, hr, hst, wsd = hdiv[n]
             timed(f"divmod_{2 * n}_{n}",
@@ -619,7 +622,20 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
 
     h2d_gbs = copy_gbs(lambda: probe_d.copy_(probe_h, non_blocking=True))
     d2h_gbs = copy_gbs(lambda: probe_h.copy_(probe_d, non_blocking=True))
-    del probe_h, probe_d
+    # both directions at once (as the step's copies run): bytes moved both
+    # ways per second
+    probe_h2 = torch.empty_like(probe_h).pin_memory()
+    probe_d2 = torch.empty_like(probe_d)
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def both():
+        with torch.cuda.stream(s_in):
+            probe_d.copy_(probe_h, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            probe_h2.copy_(probe_d2, non_blocking=True)
+
+    both_gbs = 2 * copy_gbs(both)
+    del probe_h, probe_d, probe_h2, probe_d2
 
     step()
     torch.cuda.synchronize()
@@ -637,7 +653,9 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "path": "bigint_host_async + bigint_host_sync (C ABI, pinned host buffers, copies "
                     "overlapped with kernels)",
-            "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
+            "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1),
+                              "both_directions_at_once": round(both_gbs, 1)},
+            "copy_bound_ms_per_step": round((h2d + d2h) / (both_gbs * 1e9) * 1e3, 1),
             "calls_ms": {k: round(v / steps, 2) for k, v in calls_ms.items()}}
 
 def run_batched(args):
