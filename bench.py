@@ -53,7 +53,7 @@ def parse():
                         "batch in one persistent launch vs one launch per size class; "
                         "serving: continuous batching vs per-request launches")
     p.add_argument("--batch-ops", type=int, default=200000)
-    p.add_argument("--requests", type=int, default=20000)
+    p.add_argument("--requests", type=int, default=100000)
     p.add_argument("--rates", default="5000,20000,50000,100000,200000")
     return p.parse_args()
 
