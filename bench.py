@@ -330,6 +330,11 @@ def main():
 
     mul_events = {n: [] for n in sizes}
     add_events = {n: [] for n in sizes}
+    # the three divisions are independent and none fills the GPU to its end
+    # (2^20 / 2^19 bits: 256 one-SM instances, two waves on 152 SMs), so they
+    # run side by side on streams of their own, the largest first: the
+    # smaller ones take the SMs the larger ones leave idle in their last wave
+    div_streams = [torch.cuda.Stream(device=dev) for _ in DIV]
 
     def one_step(record):
         launches = 0
@@ -354,10 +359,20 @@ def main():
                 e3.record(stream)
                 mul_events[n].append((e2, e3))
             launches += 3
-        for n, batch in DIV:
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        joins = []
+        for (n, batch), ds in zip(sorted(DIV, reverse=True), div_streams):
             D = divs[n]
-            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"])
+            ds.wait_event(fork)
+            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"],
+                      stream=ds)
+            j = torch.cuda.Event()
+            j.record(ds)
+            joins.append(j)
             launches += 1
+        for j in joins:
+            stream.wait_event(j)
         return launches
 
     for _ in range(max(args.warmup, 3)):
