@@ -484,10 +484,11 @@ __device__ void tc_release(TcCtx &c) {
 // with nx <= ny, nout <= nx + ny, x, y, out in global memory (out disjoint
 // from x and y) and c.sm holding layout<NT, G>(nx, ny).total bytes.
 //
-// Band mode (lo > 0): tiles whose limbs all lie below limb lo are skipped;
-// limbs below the first computed tile (L0 = 16 c0 <= lo) are left untouched,
-// and out[L0..nout) holds (x y - D) / B^L0 + 2^32 with D the skipped part of
-// the convolution, |D| < 2^31 B^L0.  So for h >= lo + 2 the value
+// Band mode (lo > 0): the tiles start at the column that holds limb lo
+// (limb L0 = 16 floor(lo / 16) <= lo), so no column below it is computed;
+// limbs below L0 are left untouched, and out[L0..nout) holds
+// (x y - D) / B^L0 + 2^32 with D the skipped part of the convolution,
+// |D| < 2^31 B^L0 / 255 (every column sum is below 2^31 in magnitude).  So for h >= lo + 2 the value
 // floor(out / B^(h - L0)) is floor(x y / B^h) or one more, and never wraps
 // while x y + B^h < B^nout.
 //
@@ -532,7 +533,11 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   __syncthreads();
 
   int L0 = -1;  // first limb of the first computed tile
-  for (int c0 = 0; 16 * c0 < nout; c0 += NT) {
+  // band mode: tiles anchored at the column of limb lo rather than at 0, so
+  // that the columns below it (a whole tile of them, or most of one) are
+  // not computed
+  const int cfirst = lo > 0 ? lo / 16 : 0;
+  for (int c0 = cfirst; 16 * c0 < nout; c0 += NT) {
     int W = Ly.ctot - c0;
     if (W > NT) W = NT;
     const int need = (nout - 16 * c0 + 15) / 16;  // columns holding limbs < nout
