@@ -156,3 +156,39 @@ def test_hankel_rows_from_the_staging_copies():
             src = D1 if s & 1 else D0
             row = halves(src[(s >> 1):(s >> 1) + 4])
             assert row == [0x6600 + dig(ytop - s - w) for w in range(8)], (s, eb, G)
+
+
+def test_group_partial_sums_fit_fp32():
+    """An accumulator sums G blocks of 128 digit products between drains:
+    at most G 2^21 <= 2^24 in magnitude for G <= 8, the range in which fp32
+    holds every integer; the all +-128 byte pattern 0x7F80... reaches 2^24
+    with G = 8, so the bound is tight."""
+    def group_max(x_limbs, y_limbs, G):
+        dx = np.array([digit(int(v), int(x_limbs[i - 1]) if i else 0, k)
+                       for i, v in enumerate(x_limbs) for k in range(8)], dtype=np.int64)
+        dy = np.array([digit(int(v), int(y_limbs[i - 1]) if i else 0, k)
+                       for i, v in enumerate(y_limbs) for k in range(8)], dtype=np.int64)
+        nb = len(dy) // 128
+        best = 0
+        for c in range(nb + len(dx) // 128):      # output column c, coefficient 128 c + t
+            for e0 in range(0, nb, G):            # a group of blocks e0 .. e0 + G - 1
+                for t in (0, 63, 127):
+                    acc = 0
+                    for e in range(e0, min(e0 + G, nb)):
+                        for i in range(128):
+                            xi = 128 * (c - e) + i
+                            yi = 128 * e + t - i
+                            if 0 <= xi < len(dx) and 0 <= yi < len(dy):
+                                acc += int(dx[xi]) * int(dy[yi])
+                    best = max(best, abs(acc))
+        return best
+
+    pat = [0x7F807F807F807F80] * 128  # 8 blocks of digits alternating -128 / +128
+    assert group_max(pat, pat, 8) == 1 << 24
+    rng = np.random.default_rng(3)
+    x = [int(v) for v in rng.integers(0, 1 << 63, 128, dtype=np.uint64)]
+    y = [int(v) for v in rng.integers(0, 1 << 63, 128, dtype=np.uint64)]
+    for G in (4, 7, 8):
+        assert group_max(x, y, G) <= G << 21 <= 1 << 24
+    assert float(np.float32(1 << 24)) == 1 << 24
+    assert float(np.float32((1 << 24) - 1)) == (1 << 24) - 1
