@@ -10,8 +10,10 @@
 // no cudaMalloc, cudaFree or any allocating library routine.
 //
 // In host code the array's name is only a host-side stand-in, not a device
-// address, so the address is looked up once per device with
-// cudaGetSymbolAddress and then passed to the existing division kernels.
+// address, so the address is looked up with cudaGetSymbolAddress once per
+// device (again only if that device's context was destroyed and created
+// anew, which can move the array) and then passed to the existing division
+// kernels.
 // Batches whose scratch does not fit the array are processed in consecutive
 // launches on the caller's stream, as many instances per launch as fit.
 #include <mutex>
@@ -31,19 +33,63 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB per device
 static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_SCRATCH_BYTES / 8];
 
 constexpr int MAX_DEVICES = 64;
-void *g_scratch_addr[MAX_DEVICES] = {};
+// Per device: the scratch array's device address and the id of the context
+// it was looked up in.  The array lives in the library's module, which is
+// loaded once per context: after cudaDeviceReset (or any other way the
+// device's context is destroyed and created again) the module is loaded
+// again and the array may sit at another address, so a lookup is valid only
+// for the context it was made in.
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  void *addr;
+};
+ScratchEntry g_scratch[MAX_DEVICES] = {};
 std::mutex g_scratch_mutex;
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device), or nullptr if the lookup failed.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Unique id of the context current on this thread (0 if none), through the
+// driver entry points the runtime hands out (no link against libcuda).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (get_current == nullptr || get_id == nullptr) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess)
+      return 0;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context of device
+// `dev` (current on this thread), looked up with cudaGetSymbolAddress the
+// first time the library meets that context; nullptr if the lookup failed.
 void *scratch_address(int dev) {
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
+  // makes the device's primary context current (and creates it if needed),
+  // so that there is a context whose id identifies the lookup
+  if (cudaSetDevice(dev) != cudaSuccess) return nullptr;
+  const unsigned long long id = current_context_id();
+  ScratchEntry &e = g_scratch[dev];
+  if (e.addr == nullptr || id == 0 || e.ctx_id != id) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
-    g_scratch_addr[dev] = p;
+    e.addr = p;
+    e.ctx_id = id;
   }
-  return g_scratch_addr[dev];
+  return e.addr;
 }
 
 }  // namespace

@@ -4,7 +4,10 @@ memory (its scratch is the library's own fixed __device__ array).
 Collected last on purpose.  It calls the entry point through the C ABI and
 checks it against bigint_divmod (the workspace entry point) on two calls in
 a row with different inputs, including a batch larger than one scratch-sized
-launch, so that stale scratch contents or a wrong chunk offset would show.
+launch, so that stale scratch contents or a wrong chunk offset would show,
+and a shape large enough (2048 / 1024 limbs) for the division kernel that
+runs its products on the tensor cores, which is also compared with the
+oracle.
 """
 import ctypes
 
@@ -32,7 +35,7 @@ def call_noalloc(L, u, v):
     return q, r, st
 
 
-def test_noalloc_matches_workspace_entry_point():
+def test_noalloc_matches_workspace_entry_point(orc):
     import torch
 
     import paper_2607_28897_gb300 as bi
@@ -43,8 +46,10 @@ def test_noalloc_matches_workspace_entry_point():
     per = bi.divmod_workspace_bytes(1, 1024, 512)
     cases = [inputs.config_div(64, 50, seed=21),
              # more instances than one 32 MiB scratch launch holds
-             inputs.config_div(512, (32 << 20) // per * 2 + 37, seed=22)]
-    for u, v in cases:  # two calls in a row
+             inputs.config_div(512, (32 << 20) // per * 2 + 37, seed=22),
+             # products on the tensor cores inside the division kernel
+             inputs.config_div(1024, 6, seed=23)]
+    for k, (u, v) in enumerate(cases):  # calls in a row, each after the last
         du, dv = to_dev(u), to_dev(v)
         q1, r1, s1 = call_noalloc(L, du, dv)
         q2, r2, s2 = bi.divmod(du, dv)
@@ -53,3 +58,7 @@ def test_noalloc_matches_workspace_entry_point():
         assert np.array_equal(to_host(r1), to_host(r2))
         assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
         assert not s1.cpu().numpy().any()
+        if k == 2:
+            oq, orr, ost = orc.batch_divmod(u, v)
+            assert np.array_equal(to_host(q1), oq) and np.array_equal(to_host(r1), orr)
+
