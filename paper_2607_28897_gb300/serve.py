@@ -55,15 +55,41 @@ def make_workload(seed: int, count: int, rate: float, device="cuda", mix_mul=0.5
 
 
 class _InFlight:
-    def __init__(self, idx, batch, dev_in, dev_out, host_out, status, done, nbytes):
+    def __init__(self, idx, batch, dev_in, dev_out, host_out, status, done, nbytes, stream):
         self.idx, self.batch, self.dev_in, self.dev_out = idx, batch, dev_in, dev_out
         self.host_out, self.status, self.done, self.nbytes = host_out, status, done, nbytes
+        self.stream = stream
+
+
+def _sub_batch(w: Workload, lo: int, hi: int):
+    """Descriptors of requests [lo, hi) re-based onto their own input and
+    output pools; returns (ops, input base, input limbs, output limbs)."""
+    idx = np.arange(lo, hi)
+    sub = w.ops[idx].copy()
+    base = int(w.ops["a"][lo])
+    in_limbs = int(w.ops["b"][hi - 1] + w.ops["nb"][hi - 1]) - base
+    sub["a"] -= base
+    sub["b"] -= base
+    o = np.concatenate([[0], np.cumsum(w.out_limbs[idx])[:-1]])
+    sub["o1"] = o
+    nq = np.maximum(sub["na"] - sub["nb"] + 1, 1)
+    sub["o2"] = np.where(sub["op"] == OP_DIVMOD, o + nq, 0)
+    return sub, base, in_limbs, int(w.out_limbs[idx].sum())
 
 
 def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048,
                    keep_results=False):
     """Serves the workload; returns a dict with throughput, p50/p99 latency,
-    per-request statuses and (optionally) the results."""
+    per-request statuses, the number of batches launched and (optionally)
+    the results.
+
+    Admission: every request that has arrived joins the next batch while a
+    stream has no batch in flight and the batch's device bytes -- operands,
+    results and the batch workspace (the division scratch that holds the
+    Newton iterates) -- fit the HBM budget next to the batches in flight.
+    A batch over the budget is halved until it fits; with nothing in
+    flight, a single request is admitted even if it alone exceeds the
+    budget (nothing else could make room for it)."""
     import torch
 
     load()
@@ -76,9 +102,7 @@ def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048
     latency = np.zeros(n)
     statuses = np.zeros(n, dtype=np.int32)
     results = {} if keep_results else None
-    inflight, in_use, nxt, done_count, si = [], 0, 0, 0, 0
-    a_off = w.ops["a"]
-    in_end = w.ops["b"] + w.ops["nb"]
+    inflight, in_use, nxt, done_count, batches, peak = [], 0, 0, 0, 0, 0
     while done_count < n:
         now = time.perf_counter() - t0
         # retire finished batches
@@ -98,28 +122,26 @@ def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048
             else:
                 still.append(f)
         inflight = still
-        # admit: every request that has arrived, while a slot and budget are free
-        if nxt < n and w.arrival[nxt] <= now and len(inflight) < streams:
+        # admit: every request that has arrived, while a stream is free and
+        # the batch fits the budget
+        busy = {id(f.stream) for f in inflight}
+        free = [s for s in ss if id(s) not in busy]
+        if nxt < n and w.arrival[nxt] <= now and free:
             hi = int(np.searchsorted(w.arrival, now, side="right"))
             hi = min(hi, nxt + max_batch)
-            idx = np.arange(nxt, hi)
-            sub = w.ops[idx].copy()
-            base = int(a_off[idx[0]])
-            in_limbs = int(in_end[idx[-1]]) - base
-            sub["a"] -= base
-            sub["b"] -= base
-            o = np.concatenate([[0], np.cumsum(w.out_limbs[idx])[:-1]])
-            sub["o1"] = o
-            nq = np.maximum(sub["na"] - sub["nb"] + 1, 1)
-            sub["o2"] = np.where(sub["op"] == OP_DIVMOD, o + nq, 0)
-            out_limbs = int(w.out_limbs[idx].sum())
-            io_bytes = 8 * (in_limbs + out_limbs)
-            if in_use + io_bytes <= budget_bytes or not inflight:
-                s = ss[si % streams]
-                si += 1
+            while True:
+                sub, base, in_limbs, out_limbs = _sub_batch(w, nxt, hi)
+                batch = Batch(sub, allocate=False)
+                nbytes = 8 * (in_limbs + out_limbs) + batch.workspace_bytes
+                if in_use + nbytes <= budget_bytes or hi - nxt == 1:
+                    break
+                batch.close()
+                hi = nxt + (hi - nxt) // 2
+            if in_use + nbytes <= budget_bytes or not inflight:
+                s = free[0]
+                idx = np.arange(nxt, hi)
                 with torch.cuda.stream(s):
-                    batch = Batch(sub, stream=s)
-                    nbytes = io_bytes + batch.workspace_bytes
+                    batch.allocate(stream=s)
                     dev_in = torch.empty(in_limbs, dtype=torch.int64, device="cuda")
                     dev_in.copy_(w.pool[base:base + in_limbs], non_blocking=True)
                     dev_out = torch.empty(out_limbs, dtype=torch.int64, device="cuda")
@@ -134,10 +156,13 @@ def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048
                     done = torch.cuda.Event(enable_timing=True)
                     done.record(s)
                 inflight.append(_InFlight(idx, batch, dev_in, dev_out, host_out, host_st, done,
-                                          nbytes))
+                                          nbytes, s))
                 in_use += nbytes
+                peak = max(peak, in_use)
+                batches += 1
                 nxt = hi
                 continue
+            batch.close()
         if not inflight and nxt < n and w.arrival[nxt] > now:
             time.sleep(min(w.arrival[nxt] - now, 0.001))
         elif inflight:
@@ -146,7 +171,8 @@ def run_continuous(w: Workload, budget_bytes=64 << 30, streams=3, max_batch=2048
     return {"requests": n, "seconds": total, "throughput": n / total,
             "p50_ms": float(np.percentile(latency, 50) * 1e3),
             "p99_ms": float(np.percentile(latency, 99) * 1e3),
-            "status": statuses, "results": results}
+            "status": statuses, "results": results, "batches": batches,
+            "peak_bytes_in_flight": peak}
 
 
 def run_per_request(w: Workload, limit: int | None = None):
@@ -194,10 +220,11 @@ class Server:
     stay on the device until the caller copies them).
 
     Pending requests are launched as one ragged batch (persistent form, one
-    launch) when a stream slot is free and the batch's operand, result and
-    workspace bytes fit the HBM budget next to the batches in flight
-    (admission; a request that alone exceeds the budget is refused with
-    BigIntError).  Batches on different streams overlap on the GPU."""
+    launch) on a stream with no batch in flight, when the batch's operand,
+    result and workspace bytes fit the HBM budget next to the batches in
+    flight (admission; a request whose operands and results alone exceed the
+    budget is refused with BigIntError).  Batches on different streams
+    overlap on the GPU."""
 
     def __init__(self, budget_bytes: int = 64 << 30, streams: int = 3, max_batch: int = 2048,
                  device="cuda"):
@@ -208,7 +235,8 @@ class Server:
         self.max_batch = max_batch
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
-        self._next_stream = 0
+        self.batches_launched = 0
+        self.peak_in_use = 0
         self._pending = []   # (ticket, op, a, b)
         self._inflight = []  # dicts: tickets, event, bytes, keep-alive tensors
         self._done = {}      # ticket -> tuple of result tensors
@@ -269,26 +297,35 @@ class Server:
                 take.append((t, op, a, b))
                 in_limbs += add_in
                 out_limbs += add_out
-            if 8 * (in_limbs + out_limbs) + self._in_use > self.budget and self._inflight:
+            # the batch's workspace (division scratch) counts against the
+            # budget too: drop requests from the end until everything fits
+            while True:
+                ops = np.zeros(len(take), dtype=op_dtype())
+                pos = oo = 0
+                for k, (t, op, a, b) in enumerate(take):
+                    o1, o2 = self._out_limbs(op, a.numel(), b.numel())
+                    ops[k] = (op, a.numel(), b.numel(), 0, pos, pos + a.numel(), oo,
+                              oo + o1 if op == OP_DIVMOD else 0)
+                    pos += a.numel() + b.numel()
+                    oo += o1 + o2
+                batch = Batch(ops, device=self.device, allocate=False)
+                nbytes = 8 * (pos + oo) + batch.workspace_bytes
+                if nbytes + self._in_use <= self.budget or len(take) == 1:
+                    break
+                batch.close()
+                take = take[: len(take) // 2]
+            if nbytes + self._in_use > self.budget and self._inflight:
+                batch.close()
                 return  # wait for a batch to retire
             self._pending = self._pending[len(take):]
-            ops = np.zeros(len(take), dtype=op_dtype())
-            ia = ib = oo = 0
-            pos = 0
-            for k, (t, op, a, b) in enumerate(take):
-                o1, o2 = self._out_limbs(op, a.numel(), b.numel())
-                ops[k] = (op, a.numel(), b.numel(), 0, pos, pos + a.numel(), oo,
-                          oo + o1 if op == OP_DIVMOD else 0)
-                pos += a.numel() + b.numel()
-                oo += o1 + o2
-            s = self.streams[self._next_stream % len(self.streams)]
-            self._next_stream += 1
+            busy = {id(f["stream"]) for f in self._inflight}
+            s = next(x for x in self.streams if id(x) not in busy)
             with torch.cuda.stream(s):
+                batch.allocate(device=self.device, stream=s)
                 pool = torch.cat([x.to(self.device, dtype=torch.int64, non_blocking=True).view(-1)
                                   for _, _, a, b in take for x in (a, b)])
                 out = torch.empty(max(oo, 1), dtype=torch.int64, device=self.device)
                 status = torch.empty(len(take), dtype=torch.int32, device=self.device)
-                batch = Batch(ops, device=self.device, stream=s)
                 batch.launch(pool, out, status, mode=BATCH_PERSISTENT, stream=s)
                 ev = torch.cuda.Event()
                 ev.record(s)
@@ -298,9 +335,10 @@ class Server:
                 o1, o2 = self._out_limbs(op, a.numel(), b.numel())
                 r1 = out[int(o["o1"]):int(o["o1"]) + o1]
                 results[t] = (r1, out[int(o["o2"]):int(o["o2"]) + o2]) if op == OP_DIVMOD else (r1,)
-            nbytes = 8 * (in_limbs + out_limbs) + batch.workspace_bytes
             self._in_use += nbytes
-            self._inflight.append({"event": ev, "results": results, "bytes": nbytes,
+            self.peak_in_use = max(self.peak_in_use, self._in_use)
+            self.batches_launched += 1
+            self._inflight.append({"event": ev, "results": results, "bytes": nbytes, "stream": s,
                                    "keep": (pool, out, status, batch)})
 
     def poll(self, ticket: int) -> bool:

@@ -9,27 +9,31 @@ from helpers import to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 
-def oracle_results(orc, ops, pool):
-    """Expected output pool and statuses from the oracle, op by op."""
-    out = {}
-    st = np.zeros(len(ops), dtype=np.int32)
-    for i, o in enumerate(ops):
+def oracle_results(orc, ops, pool, threads=16):
+    """Expected output pool and statuses from the oracle, op by op (each
+    operation computed alone; the oracle's C calls release the GIL, so a
+    thread pool runs them side by side)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(i):
+        o = ops[i]
         a = pool[o["a"]:o["a"] + o["na"]]
         b = pool[o["b"]:o["b"] + o["nb"]]
         if o["op"] == 1:
             r, c = orc.add(a, b)
-            out[i] = (r,)
-            st[i] = c
-        elif o["op"] == 2:
+            return (r,), c
+        if o["op"] == 2:
             r, c = orc.sub(a, b)
-            out[i] = (r,)
-            st[i] = c
-        elif o["op"] == 3:
-            out[i] = (orc.mul(a, b),)
-        else:
-            q, r, s = orc.divmod_(a, b)
-            out[i] = (q, r)
-            st[i] = {0: 0, 2: -2, 1: -7}[s]
+            return (r,), c
+        if o["op"] == 3:
+            return (orc.mul(a, b),), 0
+        q, r, s = orc.divmod_(a, b)
+        return (q, r), {0: 0, 2: -2, 1: -7}[s]
+
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, range(len(ops))))
+    out = {i: r for i, (r, _) in enumerate(res)}
+    st = np.array([s for _, s in res], dtype=np.int32)
     return out, st
 
 
@@ -155,3 +159,56 @@ def test_batch_tensor_cores_equal_integer(orc, mode):
     check(ops, p0, s0, exp, exp_st)
     assert np.array_equal(s0, s2)
     check(ops, p2, s2, exp, exp_st)
+
+
+def config4_slice(count, seed_ops=4, seed_pool=5):
+    """The first `count` operations of the batched workload (200k ragged
+    instances, 2^15..2^19 bits, 40 % mul / 15 % add / 15 % sub / 30 %
+    divmod; the same seeds as the bench) followed by four operations at the
+    largest sizes: 8192 x 8192-limb products, 16384 / 8192-limb divisions
+    (one with a divisor of top limb 1) and an 8192-limb addition."""
+    from paper_2607_28897_gb300 import inputs
+
+    ops_all, _, _ = inputs.ragged_ops(seed_ops, 200000)
+    ops = ops_all[:count].copy()
+    nin = int(ops["b"][-1] + ops["nb"][-1])
+    nout = int(max(o["o2"] + o["nb"] if o["op"] == 4 else o["o1"] + (
+        o["na"] + o["nb"] if o["op"] == 3 else o["na"]) for o in ops))
+    pool = inputs.ragged_pool(seed_pool, ops, nin)
+    extra = np.zeros(4, dtype=ops.dtype)
+    shapes = [(3, 8192, 8192), (4, 16384, 8192), (4, 16384, 8192), (1, 8192, 8192)]
+    parts = [pool]
+    pos, opos = nin, nout
+    for k, (op, na, nb) in enumerate(shapes):
+        a = inputs.limbs(900 + k, 1, na, top_nonzero=True)[0]
+        b = inputs.limbs(950 + k, 1, nb, top_nonzero=True)[0]
+        if k == 2:
+            b[-1] = np.uint64(1)  # divisor just above B^(nb-1)
+        nq = na - nb + 1
+        extra[k] = (op, na, nb, 0, pos, pos + na, opos, opos + nq if op == 4 else 0)
+        parts += [a, b]
+        pos += na + nb
+        opos += (na + nb) if op == 3 else (nq + nb if op == 4 else na)
+    return np.concatenate([ops, extra]), np.concatenate(parts), opos
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_config4_slice_against_oracle(orc, mode):
+    """A slice of the batched workload at its own sizes (up to 8192-limb
+    products and 16384 / 8192-limb divisions on the tensor cores), in the
+    persistent and the per-class form, against the oracle op by op."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+
+    ops, pool, nout = config4_slice(1500)
+    assert ops["na"].max() == 16384 and (ops["op"] == 4).sum() > 100
+    exp, exp_st = oracle_results(orc, ops, pool)
+    dpool = to_dev(pool).view(-1)
+    dout = torch.zeros(nout, dtype=torch.int64, device="cuda")
+    st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+    B = bi.Batch(ops)
+    B.launch(dpool, dout, st, mode=mode)
+    torch.cuda.synchronize()
+    bi.check_timeout()
+    check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
