@@ -53,7 +53,12 @@ def parse():
                         "batch in one persistent launch vs one launch per size class; "
                         "serving: continuous batching vs per-request launches")
     p.add_argument("--batch-ops", type=int, default=200000)
-    p.add_argument("--requests", type=int, default=100000)
+    p.add_argument("--requests", type=int, default=100000,
+                   help="requests per rate of --workload serving")
+    p.add_argument("--serving-requests", type=int, default=10000,
+                   help="requests per rate of the serving block in the default line")
+    p.add_argument("--no-forms", action="store_true",
+                   help="leave the batched and serving blocks out of the default line")
     p.add_argument("--rates", default="5000,20000,50000,100000,200000")
     return p.parse_args()
 
@@ -356,7 +361,6 @@ def main():
     div_streams = [torch.cuda.Stream(device=dev) for _ in DIV]
 
     def one_step(record):
-        launches = 0
         flush.fill_(1)
         for n in sizes:
             S = sweep[n]
@@ -377,7 +381,6 @@ def main():
                 e3 = torch.cuda.Event(enable_timing=True)
                 e3.record(stream)
                 mul_events[n].append((e2, e3))
-            launches += 3
         fork = torch.cuda.Event()
         fork.record(stream)
         joins = []
@@ -389,10 +392,8 @@ def main():
             j = torch.cuda.Event()
             j.record(ds)
             joins.append(j)
-            launches += 1
         for j in joins:
             stream.wait_event(j)
-        return launches
 
     for _ in range(max(args.warmup, 3)):
         one_step(False)
@@ -408,9 +409,10 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    launches = 0
+    k0 = bi.kernel_launches()
     for _ in range(args.steps):
-        launches += one_step(True)
+        one_step(True)
+    launches = bi.kernel_launches() - k0  # every kernel the library enqueued
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -467,6 +469,24 @@ def main():
                 fn()
             row[name] = round(time_op(fn, reps=20) * 1e3, 1)
         latency[f"mul_{n}x{n}_one_product"] = row
+    # one 2^20 / 2^19-bit division alone: the step-batched form (every
+    # product one launch over the whole GPU) against one CTA per division
+    if 8192 in divs:
+        D = divs[8192]
+        u1, v1 = D["u"][1:2], D["v"][1:2]
+        q1 = torch.empty((1, 8193), dtype=torch.int64, device=dev)
+        r1 = torch.empty((1, 8192), dtype=torch.int64, device=dev)
+        s1 = torch.empty(1, dtype=torch.int32, device=dev)
+        w1 = torch.empty(bi.divmod_workspace_bytes(1, 16384, 8192), dtype=torch.uint8, device=dev)
+        row = {}
+        for name, variant in (("steps_us", 0), ("one_cta_us", 1)):
+            bi.set_variant(1, variant)
+            fn = lambda: bi.divmod(u1, v1, q=q1, r=r1, status=s1, workspace=w1, stream=stream)
+            for _ in range(2):
+                fn()
+            row[name] = round(time_op(fn, reps=5) * 1e3, 1)
+        bi.set_variant(1, 0)
+        latency["divmod_16384_8192_one_division"] = row
 
     # ---- roofline of the dominant kernel: the multiply launch at the largest
     #      size (2^19 bits), the longest launch of the step
@@ -495,12 +515,17 @@ def main():
               f" (variant {vmax}), {nmax}-limb operands, batch {sweep_batch(nmax)}")
     if vmax == 12:
         # tensor bound: 2 flops per fp16 digit product of the 8-bit schoolbook
-        # convolution, (8 n)^2 per n x n product; sustained peak because the
-        # kernel is timed inside the long step
+        # convolution, (8 n)^2 per n x n product.  The step holds the maximum
+        # SM clock (no power cap: see "clocks"), so the burst peak -- a GEMM
+        # timed alone at that clock -- is the denominator; the fraction of
+        # the sustained (power-capped) peak and of the nominal dense rate
+        # are given beside it.
         def tc_flops(n):
             return 2.0 * (8 * n) ** 2 * sweep_batch(n)
 
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        burst = float(peaks.get("bf16_tflops", 1900.0))
+        sustained = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak = burst
         achieved = tc_flops(nmax) / (mul_ms * 1e-3) / 1e12
         tc_sizes = [n for n in sizes if bi.mul_variant_for(n, n) == 12]
         tc_ms = sum(breakdown[f"mul_{n}"]["ms"] for n in tc_sizes)
@@ -512,9 +537,16 @@ def main():
                                         "base-256 digits, accumulated in fp32",
                     "frac_all_sizes": (sum(tc_flops(n) for n in tc_sizes) / (tc_ms * 1e-3) / 1e12
                                        / peak) if tc_sizes else None,
-                    "peak_basis": ("of measured: MEASURED_PEAKS.json bf16_tflops_sustained "
-                                   "(fp16 and bf16 share the nominal dense rate)")
-                    if "bf16_tflops_sustained" in peaks else "of fallback: 1700 TFLOP/s sustained"}
+                    "frac_by_size": {str(n): tc_flops(n) / (breakdown[f"mul_{n}"]["ms"] * 1e-3)
+                                     / 1e12 / peak for n in tc_sizes},
+                    "frac_of_sustained": achieved / sustained,
+                    "frac_of_nominal_2250": achieved / 2250.0,
+                    "peak_basis": ("of measured: MEASURED_PEAKS.json bf16_tflops (burst: a GEMM "
+                                   "timed alone; fp16 and bf16 share the nominal dense rate), "
+                                   "the basis for a step that held the maximum SM clock; "
+                                   "frac_of_sustained divides by bf16_tflops_sustained "
+                                   "(measured power-capped)")
+                    if "bf16_tflops" in peaks else "of fallback: 1900 TFLOP/s burst"}
     else:
         ipc, probe_mhz = bi.probe_int_throughput(0)  # IMAD.WIDE per SM per clock
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -543,6 +575,15 @@ def main():
     # ---- end to end through the C ABI with host buffers
     e2e = run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, world, dist)
 
+    # ---- the batched form (200k ragged instances) and the serving loop
+    #      (continuous batching at Poisson rates), outside the timed step
+    batched = serving = None
+    if not args.no_forms:
+        batched = batched_block(torch, bi, args.batch_ops, 3, rank, world, dist, dev)
+        if world == 1:
+            serving = serving_block(torch, bi, [float(r) for r in args.rates.split(",")],
+                                    args.serving_requests, 1000)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -558,7 +599,7 @@ def main():
             "data": "synthetic", "config": workload_config(sizes), "roofline": roofline,
             "roofline_add": roofline_add, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
-            "latency": latency,
+            "latency": latency, "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -692,23 +733,28 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
             "copy_bound_ms_per_step": round((h2d + d2h) / (both_gbs * 1e9) * 1e3, 1),
             "calls_ms": {k: round(v / steps, 2) for k, v in calls_ms.items()}}
 
-def run_batched(args):
-    """The batched form: ragged instances (sizes log-uniform over 2^15..2^19
-    bits; 40 % mul, 15 % add, 15 % sub, 30 % divmod) in one persistent launch
-    with a device-side work queue (tuned CTA size, CUDA-graph replay) against
-    one launch per (op, size class)."""
-    import torch
+def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
+    """The batched form: `count` ragged instances (sizes log-uniform over
+    2^15..2^19 bits; 40 % mul, 15 % add, 15 % sub, 30 % divmod) in one
+    persistent launch with a device-side work queue (tuned CTA size,
+    CUDA-graph replay), against one launch per (op, size class).  With
+    several ranks the batch is split by estimated cost (ranks.partition) and
+    every rank runs its share (strong scaling of the fixed batch); times are
+    the maximum over ranks."""
+    import numpy as np
 
-    import paper_2607_28897_gb300 as bi
-    from paper_2607_28897_gb300 import inputs
+    from paper_2607_28897_gb300 import inputs, ranks
 
-    bi.load()
-    count = args.batch_ops
     ops, nin, nout = inputs.ragged_ops(4, count)
-    pool = inputs.ragged_pool(5, ops, nin, device="cuda")
-    out = torch.zeros(nout, dtype=torch.int64, device="cuda")
-    st = torch.zeros(count, dtype=torch.int32, device="cuda")
-    B = bi.Batch(ops)
+    pool = inputs.ragged_pool(5, ops, nin, device=dev or "cuda")
+    if world > 1:
+        part = ranks.partition(ops, world)[rank]
+        host_pool = pool.cpu().numpy().view(np.uint64)
+        ops, sub_pool, nout, _ = ranks.sub_batch(ops, part, host_pool)
+        pool = torch.from_numpy(sub_pool.view(np.int64)).to(dev or "cuda")
+    out = torch.zeros(max(nout, 1), dtype=torch.int64, device=pool.device)
+    st = torch.zeros(max(len(ops), 1), dtype=torch.int32, device=pool.device)
+    B = bi.Batch(ops, device=pool.device)
 
     def best_of(fn, reps):
         fn()
@@ -721,12 +767,12 @@ def run_batched(args):
             e1.record()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-        return min(times)
+        return ranks.max_over_ranks(min(times), dist, dev)
 
-    reps = max(args.steps, 1)
     t_class = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PER_CLASS), reps)
     ref = out.clone()
     t_pers = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PERSISTENT), reps)
+    same_pers = bool(torch.equal(out, ref))
     threads = B.tune(pool, out, st)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -737,16 +783,48 @@ def run_batched(args):
         with torch.cuda.graph(g, stream=s):
             B.launch(pool, out, st, stream=s)
     t_graph = best_of(lambda: g.replay(), reps)
-    same = bool(torch.equal(out, ref))
-    units = ops["na"].astype(float) * ops["nb"]
-    line = {"metric": "batched form: ragged mixed-op instances per second", "value": count / (t_graph * 1e-3),
-            "unit": "ops/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": f"{count} ragged instances, 2^15..2^19 bits log-uniform, "
-                                   "40% mul / 15% add / 15% sub / 30% divmod (n_u in [n_v, 2 n_v])"},
-            "per_class_ms": t_class, "persistent_ms": t_pers, "persistent_tuned_graph_ms": t_graph,
-            "tuned_threads": threads, "speedup_vs_per_class": t_class / t_graph,
-            "results_identical_across_forms": same}
-    print(json.dumps(line), flush=True)
+    same = same_pers and bool(torch.equal(out, ref))
+    bad_status = int((st[:len(ops)] < 0).sum().item()) if len(ops) else 0
+    del pool, out, st, ref, g
+    B.close()
+    torch.cuda.empty_cache()
+    best = min(t_pers, t_graph)
+    return {"workload": f"{count} ragged instances, 2^15..2^19 bits log-uniform, 40% mul / 15% "
+                        "add / 15% sub / 30% divmod (n_u in [n_v, 2 n_v])",
+            "ops_per_s": count / (best * 1e-3), "per_class_ms": t_class,
+            "persistent_ms": t_pers, "persistent_tuned_graph_ms": t_graph,
+            "tuned_threads": threads, "speedup_vs_per_class": t_class / best,
+            "results_identical_across_forms": same, "negative_statuses": bad_status,
+            "scaling": "strong" if world > 1 else None,
+            "ranks": world}
+
+
+def run_batched(args):
+    """The batched form alone, as its own JSON line."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import ranks
+
+    rank, local, world = ranks.world()
+    dist, dev = None, torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    bi.load()
+    blk = batched_block(torch, bi, args.batch_ops, max(args.steps, 1), rank, world, dist, dev)
+    if rank == 0:
+        line = {"metric": "batched form: ragged mixed-op instances per second",
+                "value": blk["ops_per_s"], "unit": "ops/s", "n_gpus": world,
+                "higher_is_better": True, "data": "synthetic",
+                "scaling": "strong" if world > 1 else "weak",
+                "config": {"workload": blk["workload"]}, **blk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_programs(args):
@@ -808,30 +886,43 @@ def run_programs(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_block(torch, bi, rates, requests, per_request_sample):
+    """Continuous batching against one launch per request at Poisson
+    arrival rates: throughput and p50/p99 latency per rate."""
+    from paper_2607_28897_gb300 import serve
+
+    res = []
+    for rate in rates:
+        w = serve.make_workload(41, requests, rate)
+        serve.run_continuous(serve.make_workload(42, 200, rate))  # warm-up
+        c = serve.run_continuous(w)
+        p = serve.run_per_request(w, limit=min(requests, per_request_sample))
+        res.append({"rate": rate,
+                    "continuous": {k: c[k] for k in ("throughput", "p50_ms", "p99_ms", "batches")},
+                    "continuous_negative_statuses": int((c["status"] < 0).sum()),
+                    "per_request": {k: p[k] for k in ("throughput", "p50_ms", "p99_ms")},
+                    "per_request_sample": p["requests"]})
+        del w
+        torch.cuda.empty_cache()
+    return {"workload": f"{requests} requests per rate, Poisson arrivals, 50% mul / 50% divmod, "
+                        "sizes 2^15..2^19 bits log-uniform, HBM budget 64 GiB",
+            "rates": res}
+
+
 def run_serving(args):
     """Continuous batching against per-request launches at Poisson arrival
     rates; throughput and p50/p99 latency."""
     import torch
 
     import paper_2607_28897_gb300 as bi
-    from paper_2607_28897_gb300 import serve
 
     bi.load()
-    res = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        w = serve.make_workload(41, args.requests, rate)
-        serve.run_continuous(serve.make_workload(42, 200, rate))  # warm-up
-        c = serve.run_continuous(w)
-        p = serve.run_per_request(w, limit=min(args.requests, 5000))
-        res.append({"rate": rate, "continuous": {k: c[k] for k in ("throughput", "p50_ms", "p99_ms")},
-                    "per_request": {k: p[k] for k in ("throughput", "p50_ms", "p99_ms")},
-                    "per_request_sample": p["requests"]})
-        torch.cuda.empty_cache()
-    line = {"metric": "serving: requests/s and p50/p99 latency", "value": max(r["continuous"]["throughput"] for r in res),
+    blk = serving_block(torch, bi, [float(r) for r in args.rates.split(",")], args.requests,
+                        5000)
+    line = {"metric": "serving: requests/s and p50/p99 latency",
+            "value": max(r["continuous"]["throughput"] for r in blk["rates"]),
             "unit": "req/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": f"{args.requests} requests per rate, 50% mul / 50% divmod, "
-                                   "sizes 2^15..2^19 bits log-uniform, HBM budget 64 GiB"},
-            "rates": res}
+            "config": {"workload": blk["workload"]}, **blk}
     print(json.dumps(line), flush=True)
 
 

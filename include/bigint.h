@@ -73,13 +73,18 @@ int bigint_sub(const uint64_t *a, const uint64_t *b, uint64_t *out,
                uint8_t *borrow_out, int64_t count, int32_t n, void *stream);
 
 /* ---- multiplication (Sec. V-B, Fig. 5) ----------------------------------
- * out = a * b, the FULL product of na + nb limbs per instance.  The
- * convolution C_k = sum_{i+j=k} a_i b_j (Sec. V-B) is computed by column
- * blocks ("chunks") with a balanced assignment of chunks to threads (Fig. 5
- * threadConv: a rising chunk paired with a falling one), each digit product
- * accumulated by one 32x32->64-bit multiply-add with deferred carries; each
- * chunk's digits and overflow word (Fig. 5 combineQ) are finished by one
- * carry-scan addition (Fig. 5 bmulReg).
+ * out = a * b, the FULL product of na + nb limbs per instance: the
+ * schoolbook convolution C_k = sum_{i+j=k} a_i b_j of Sec. V-B, exact.
+ * When the shorter operand has 256 limbs or more (and fits one SM's shared
+ * memory) the convolution runs on the tensor cores: the operands as signed
+ * base-256 digits, the convolution as fp16 matrix products (tcgen05.mma,
+ * Toeplitz blocks of one operand times shifted blocks of the other) with
+ * exact fp32 accumulation in tensor memory, the column sums turned into
+ * limbs by one carry scan per output tile (Fig. 3).  Smaller products use
+ * the integer pipes: column blocks ("chunks") with rising and falling chunks
+ * paired per thread (Fig. 5 threadConv), one 32x32->64-bit multiply-add per
+ * digit product with deferred carries, and one carry-scan addition of the
+ * chunks' digits and overflow words (Fig. 5 combineQ, bmulReg).
  * a: count*na limbs, b: count*nb limbs, out: count*(na+nb) limbs.
  * 1 <= na, nb <= BIGINT_MUL_MAX_LIMBS.                                     */
 int bigint_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
@@ -124,7 +129,13 @@ int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out,
  * holds the quotient mod B^nq and r is exact).
  * workspace: device scratch of at least bigint_divmod_workspace(count, nu,
  * nv) bytes, 256-byte aligned, owned by the caller, contents clobbered.
- * 1 <= nu, nv <= BIGINT_MAX_LIMBS.                                        */
+ * 1 <= nu, nv <= BIGINT_MAX_LIMBS.
+ * Schedule: with divisors of 128 limbs or more (and nu >= nv) every Newton
+ * step runs for all instances at once -- each product one batched launch
+ * of the multiply kernels, each linear step one small launch -- and only
+ * instances whose dividend or divisor has a zero top limb are divided one
+ * CTA each at the end; smaller divisions run one CTA per division (the
+ * paper's intragroup form).  Results are the same either way.             */
 int bigint_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q,
                   uint64_t *r, int32_t *status, int64_t count, int32_t nu,
                   int32_t nv, void *workspace, size_t workspace_bytes,
@@ -144,6 +155,9 @@ size_t bigint_divmod_workspace(int64_t count, int32_t nu, int32_t nv);
  * allocates nothing itself.
  * - The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The lookup is repeated only when the device's context has been
+ *   destroyed and created again (cudaDeviceReset), which can move the
+ *   array.
  * - Batches larger than the array holds run as consecutive launches on
  *   `stream`; a shape whose single instance needs more scratch than the
  *   array is rejected with BIGINT_ENOMEM.
@@ -341,12 +355,16 @@ int bigint_host_sync(void);
  *   results.  Needs the shorter operand to fit shared memory (about 10700
  *   limbs; otherwise variant 8).  One persistent CTA per SM, which holds
  *   all of the SM's tensor memory while it runs.
- * op 1 = division (divmod and shinv):
- *   variant 0 (default) or 1: operands of 1536 limbs and more run in a
- *   kernel that holds its SM's tensor memory and computes products whose
+ * op 1 = division (divmod, shinv, divmod_inv):
+ *   variant 0 (default): bigint_divmod on divisors of 128 limbs or more in
+ *   the step-batched form (see bigint_divmod), everything else as variant 1
+ *   variant 1: one CTA per division; operands of 1536 limbs and more run in
+ *   a kernel that holds its SM's tensor memory and computes products whose
  *   shorter operand has at least 256 limbs on the tensor cores (as variant
  *   12 of the multiply); smaller divisions use the integer products
- *   variant 2: integer products (blk_mul) for every division
+ *   variant 2: one CTA per division, integer products (blk_mul) only
+ *   variant 3: as 0, with the step-batched form for divisors of 8 limbs
+ *   and more
  * op 2 = ragged batches (bigint_batch_*, for batches created afterwards):
  *   variant 0 (default) or 1: a batch with multiplications or divisions
  *   whose products have a shorter operand of 256 limbs or more runs them in
@@ -365,6 +383,25 @@ int bigint_set_variant(int op, int variant);
  * the tensor-core schedule, which hands work between threads and the
  * tensor cores through shared-memory barriers.                              */
 int bigint_check_timeout(void);
+
+/* Sets the cycle limit of the device-side waits of the tensor-core products
+ * for every launch from now on: cycles > 0 the limit, 0 the default (about
+ * one second).  cycles < 0 injects a timeout for testing: every such wait
+ * first waits for the tensor-core work it guards, then spins for -cycles
+ * cycles on a flag that nothing sets and gives up, so that a product stops
+ * as at a real timeout (BIGINT_ETIMEOUT from bigint_check_timeout and in a
+ * division's status, tensor memory released, the device usable
+ * afterwards).  An ordinary product cannot be made to time out with a low
+ * positive limit: its waits find the work done at their first probe.  The
+ * waits that guard the release of tensor memory always keep the full
+ * limit.  Synchronous; process-wide; not thread-safe.  The paper has no
+ * counterpart (its kernels have no such waits).                            */
+int bigint_set_wait_limit(long long cycles);
+
+/* Number of kernels the library has launched in this process so far (every
+ * launch of every entry point, counted when it is enqueued), so that a
+ * caller can report how many kernels a piece of work took. */
+unsigned long long bigint_kernel_launches(void);
 
 /* The multiply variant (1..12) a full na x nb product runs with the current
  * settings (default choice, tuning table, fallbacks), so that measurements

@@ -18,6 +18,7 @@ __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "mul_split", "mul_split_workspace_bytes",
     "divmod", "divmod_noalloc", "divmod_inv", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
+    "set_wait_limit", "check_timeout",
     "host_workspace_bytes", "add_host", "sub_host", "mul_host", "divmod_host", "host_sync",
     "add_chain", "poly", "poly_workspace_bytes",
     "OK", "EINVAL", "EDIVZERO", "ENOMEM", "ETIMEOUT", "EINTERNAL", "ECUDA", "ERANGE",
@@ -66,6 +67,8 @@ SIGNATURES = {
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
     "bigint_check_timeout": ([], ctypes.c_int),
+    "bigint_set_wait_limit": ([ctypes.c_longlong], ctypes.c_int),
+    "bigint_kernel_launches": ([], ctypes.c_ulonglong),
     "bigint_host_workspace": ([ctypes.c_int, _I64, _I32, _I32], _SZ),
     "bigint_add_chain": ([_P, _P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "bigint_poly_workspace": ([_I64, _I32], _SZ),
@@ -478,6 +481,19 @@ def check_timeout() -> None:
     _check(load().bigint_check_timeout(), "bigint_check_timeout")
 
 
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(load().bigint_kernel_launches())
+
+
+def set_wait_limit(cycles: int) -> None:
+    """Cycle limit of the tensor-core products' device waits (0: the
+    default, about one second); a negative value makes every wait give up
+    after -cycles cycles on a flag nothing sets (once the work it guards has
+    finished), which tests the timeout path."""
+    _check(load().bigint_set_wait_limit(int(cycles)), "bigint_set_wait_limit")
+
+
 def probe_int_throughput(variant: int):
     """(thread operations per SM per cycle, SM MHz) of one integer form."""
     ops, mhz = ctypes.c_double(), ctypes.c_double()
@@ -503,9 +519,8 @@ class Batch:
     library; ``launch`` only enqueues device work, so it can be captured in
     a CUDA graph."""
 
-    def __init__(self, ops, device="cuda", stream=None):
+    def __init__(self, ops, device="cuda", stream=None, allocate=True):
         import numpy as np
-        import torch
 
         self.ops = np.ascontiguousarray(ops, dtype=op_dtype())
         h = ctypes.c_void_p()
@@ -513,10 +528,20 @@ class Batch:
                "bigint_batch_create")
         self._h = h
         self.workspace_bytes = int(load().bigint_batch_workspace(h))
+        self.workspace = None
+        if allocate:
+            self.allocate(device, stream)
+
+    def allocate(self, device="cuda", stream=None):
+        """Allocates the device workspace (``workspace_bytes``, known from the
+        host-side plan alone) and uploads the plan into it."""
+        import torch
+
         self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
                                      device=device)
-        _check(load().bigint_batch_upload(h, self.workspace.data_ptr(), self.workspace.numel(),
-                                          _stream_ptr(stream)), "bigint_batch_upload")
+        _check(load().bigint_batch_upload(self._h, self.workspace.data_ptr(),
+                                          self.workspace.numel(), _stream_ptr(stream)),
+               "bigint_batch_upload")
 
     def launch(self, in_pool, out_pool, status=None, mode=BATCH_PERSISTENT, stream=None):
         rc = load().bigint_batch_launch(self._h, in_pool.data_ptr(), out_pool.data_ptr(),

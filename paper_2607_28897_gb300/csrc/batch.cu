@@ -291,7 +291,9 @@ int batch_configure(bigint_batch *B) {
   int per_sm = 1;
   int rc = occupancy(P.tc, P.threads, P.smem_words, &per_sm);
   if (rc != BIGINT_OK) return rc;
-  P.ctas = B->sms * per_sm;
+  // no more CTAs than operations: each resident CTA holds a division scratch
+  // region of the workspace, which a small batch should not pay for
+  P.ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->sms * per_sm, n));
   B->max_ctas = P.ctas;
   // per-class launches
   B->classes.clear();
@@ -430,5 +432,10 @@ int batch_retune(bigint_batch *B, int threads) {
 }
 
 void batch_destroy(bigint_batch *B) { delete B; }
+
+// The batch kernel's own record of tensor-core products that gave up at a
+// wait limit, and its wait limit (see tcm::take_timeout_here).
+int batch_take_timeout() { return tcm::take_timeout_here(); }
+int batch_set_wait_limit(long long cycles) { return tcm::set_wait_limit_here(cycles); }
 
 }  // namespace bigint

@@ -2,9 +2,15 @@
 //
 // Host-side argument checks and dispatch only; every arithmetic step runs in
 // the kernels of addsub.cu, mul.cu and divmod.cu.
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
+
+namespace bigint {
+static std::atomic<unsigned long long> g_kernel_launches{0};
+void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace bigint
 
 namespace bigint {
 int launch_addsub(bool sub, const uint64_t *a, const uint64_t *b, uint64_t *out,
@@ -19,6 +25,12 @@ int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
 int programs_take_timeout();
+int div_take_timeout();
+int batch_take_timeout();
+int tc_set_wait_limit(long long cycles);
+int div_set_wait_limit(long long cycles);
+int programs_set_wait_limit(long long cycles);
+int batch_set_wait_limit(long long cycles);
 int launch_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry,
                      int64_t count, int n, int k, cudaStream_t st);
 size_t poly_workspace(int64_t count, int n);
@@ -28,7 +40,6 @@ size_t host_workspace(int op, int64_t chunk, int na, int nb);
 int host_run(int op, const uint64_t *in0, const uint64_t *in1, uint64_t *out0, uint64_t *out1,
              void *aux, int64_t count, int na, int nb, void *workspace, size_t bytes, bool sync);
 int host_sync();
-int div_take_timeout();
 int div_set_variant(int v);
 int batch_set_variant(int v);
 int probe_int_throughput(int variant, double *ops, double *mhz);
@@ -272,9 +283,28 @@ int bigint_host_async(int op, const uint64_t *a, const uint64_t *b, uint64_t *ou
 int bigint_host_sync(void) { return host_sync(); }
 
 int bigint_check_timeout(void) {
-  const int a = tc_take_timeout(), b = div_take_timeout(), c = programs_take_timeout();
-  if (a == BIGINT_ECUDA || b == BIGINT_ECUDA || c == BIGINT_ECUDA) return BIGINT_ECUDA;
-  return a != BIGINT_OK ? a : (b != BIGINT_OK ? b : c);
+  // every translation unit that launches tensor-core products keeps its own
+  // record: ask them all (each read clears it)
+  const int rc[4] = {tc_take_timeout(), div_take_timeout(), programs_take_timeout(),
+                     batch_take_timeout()};
+  int out = BIGINT_OK;
+  for (int x : rc) {
+    if (x == BIGINT_ECUDA) return BIGINT_ECUDA;
+    if (x != BIGINT_OK) out = x;
+  }
+  return out;
+}
+
+unsigned long long bigint_kernel_launches(void) {
+  return g_kernel_launches.load(std::memory_order_relaxed);
+}
+
+int bigint_set_wait_limit(long long cycles) {
+  const int rc[4] = {tc_set_wait_limit(cycles), div_set_wait_limit(cycles),
+                     programs_set_wait_limit(cycles), batch_set_wait_limit(cycles)};
+  for (int x : rc)
+    if (x != BIGINT_OK) return x;
+  return BIGINT_OK;
 }
 
 int bigint_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_t *carry_out,

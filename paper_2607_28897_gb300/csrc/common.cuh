@@ -79,6 +79,14 @@ __device__ __forceinline__ void st_stream2(uint64_t *p, ulonglong2 v) {
     if (e__ != cudaSuccess) return BIGINT_ECUDA; \
   } while (0)
 
+namespace bigint {
+// Counts the kernel launches the library enqueues (bigint_kernel_launches).
+void count_launch();
+}  // namespace bigint
+
+// Called right after every kernel launch of the library: counts it and
+// reports a launch error.
 static inline int bigint_launch_status() {
+  bigint::count_launch();
   return cudaPeekAtLastError() == cudaSuccess ? BIGINT_OK : BIGINT_ECUDA;
 }

@@ -176,6 +176,15 @@ __device__ void mul_any(const uint64_t *x, int nx, const uint64_t *y, int ny, ui
     return;
   }
   if constexpr (TC) {
+    if (tc != nullptr && tc->aborted) {
+      // a tensor-core product of this CTA gave up at a wait limit: the
+      // result is already void (the caller reports BIGINT_ETIMEOUT), so the
+      // remaining products are zero and the division runs to its end on
+      // bounded loops
+      blk_zero(out, nout);
+      __syncthreads();
+      return;
+    }
     if (tc_mul(tc, x, nx, y, ny, out, nout, smem_words, lo)) return;
   }
   if (blk_mul_smem_words<RB, Q>(nx, ny) <= smem_words) {

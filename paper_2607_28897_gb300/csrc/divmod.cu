@@ -52,27 +52,34 @@ template <int Q, bool TC> constexpr int div_max_threads() {
   return TC ? tcm::TC_CTA_THREADS : (Q >= 16 ? 512 : 640);
 }
 
+// Without a list, CTA b divides instance b (grid = count).  With a list (the
+// instances the step-batched form leaves out, divstep.cu), CTA b divides
+// instances list[b], list[b + grid], ... of the *nlist listed; CTAs beyond
+// *nlist return before they take any tensor memory.
 template <int RB, int Q, int F, bool TC>
 __global__ void __launch_bounds__(div_max_threads<Q, TC>())
     k_divmod(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, uint64_t *Qo,
              uint64_t *Ro, int32_t *status, int nu, int nv, int nq, int mode, int h_arg,
              uint64_t *ws, int64_t ws_stride, int smem_words, const uint64_t *Wg, int nwg,
-             int64_t v_stride, int64_t w_stride) {
+             int64_t v_stride, int64_t w_stride, const int32_t *list, const int *nlist) {
   extern __shared__ __align__(1024) uint32_t smem[];
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   __shared__ tcm::TcShared tsh;
-  const int64_t inst = blockIdx.x;
-  const uint64_t *v = V + inst * v_stride;
-  uint64_t *q = Qo + inst * (int64_t)nq;
-  const int hcap = mode == 1 ? h_arg : nu;
-  Work W = carve(ws + inst * ws_stride, nu, nv, hcap);
-  int st = BIGINT_OK;
+  const int64_t nwork = list != nullptr ? (int64_t)*(volatile const int *)nlist : gridDim.x;
+  if ((int64_t)blockIdx.x >= nwork) return;
   tcm::TcCtx tcc;
   tcm::TcCtx *tc = nullptr;
   if constexpr (TC) {
     tcm::tc_init<256>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
     tc = &tcc;
   }
+  for (int64_t b = blockIdx.x; b < nwork; b += gridDim.x) {
+  const int64_t inst = list != nullptr ? (int64_t)list[b] : b;
+  const uint64_t *v = V + inst * v_stride;
+  uint64_t *q = Qo + inst * (int64_t)nq;
+  const int hcap = mode == 1 ? h_arg : nu;
+  Work W = carve(ws + inst * ws_stride, nu, nv, hcap);
+  int st = BIGINT_OK;
 
   [&] {
     const int kv = blk_prec(v, nv, scr);
@@ -140,9 +147,11 @@ __global__ void __launch_bounds__(div_max_threads<Q, TC>())
 
   if constexpr (TC) {
     if (tcc.aborted) st = BIGINT_ETIMEOUT;
-    tcm::tc_release<256>(tcc);
   }
   if (status && threadIdx.x == 0) status[inst] = st;
+  __syncthreads();
+  }
+  if constexpr (TC) tcm::tc_release<256>(tcc);
 }
 
 // ---------------------------------------------------------------------------
@@ -151,26 +160,22 @@ __global__ void __launch_bounds__(div_max_threads<Q, TC>())
 // Division kernels for H >= DIV_SMALL_LIMBS run their large products on the
 // tensor cores unless switched off (bigint_set_variant(1, ...)).
 static int g_div_tc = 1;
+// Uniform divisions: the step-batched form (divstep.cu) for divisors of
+// DIV_STEP_MIN limbs and more (0), never (1, 2: one CTA per division), or
+// for every divisor of 8 limbs and more (3).
+static int g_div_steps = 0;
 
 int div_set_variant(int v) {
-  if (v < 0 || v > 2) return BIGINT_EINVAL;
+  if (v < 0 || v > 3) return BIGINT_EINVAL;
   g_div_tc = v != 2;
+  g_div_steps = v == 0 ? 0 : (v == 3 ? 2 : 1);
   return BIGINT_OK;
 }
 
 // BIGINT_ETIMEOUT if a division kernel's tensor-core product hit a wait
 // limit since the last call (synchronises the device), else BIGINT_OK.
-int div_take_timeout() {
-  BIGINT_CUDA_TRY(cudaDeviceSynchronize());
-  int v = 0;
-  BIGINT_CUDA_TRY(cudaMemcpyFromSymbol(&v, tcm::g_timeout, sizeof(int)));
-  if (v) {
-    const int zero = 0;
-    BIGINT_CUDA_TRY(cudaMemcpyToSymbol(tcm::g_timeout, &zero, sizeof(int)));
-    return BIGINT_ETIMEOUT;
-  }
-  return BIGINT_OK;
-}
+int div_take_timeout() { return tcm::take_timeout_here(); }
+int div_set_wait_limit(long long cycles) { return tcm::set_wait_limit_here(cycles); }
 
 static int div_smem_optin() {
   int dev = 0, v = 0;
@@ -180,8 +185,15 @@ static int div_smem_optin() {
   return v;
 }
 
-size_t divmod_workspace(int64_t count, int nu, int nv) {
+// Per-instance regions of the one-CTA-per-division kernel, then (for the
+// step-batched form) the list of instances it leaves to that kernel and two
+// counters; the step-batched form's own records fit inside the regions.
+static size_t cta_regions_bytes(int64_t count, int nu, int nv) {
   return (size_t)count * (size_t)ws_limbs(nu, nv, nu) * sizeof(uint64_t);
+}
+
+size_t divmod_workspace(int64_t count, int nu, int nv) {
+  return cta_regions_bytes(count, nu, nv) + ((size_t)4 * count + 255) / 256 * 256 + 256;
 }
 
 size_t shinv_workspace(int64_t count, int nv, int h) {
@@ -195,6 +207,8 @@ struct DivExtra {
   int nw = 0;
   int64_t v_stride = -1;  // -1: nv
   int64_t w_stride = 0;
+  const int32_t *list = nullptr;  // instances to divide (device), *nlist of them
+  const int *nlist = nullptr;
 };
 
 template <int RB, int Q, int F, bool TC>
@@ -239,9 +253,20 @@ static int launch_div_variant(const uint64_t *u, const uint64_t *v, uint64_t *q,
   }
   const int hcap = mode == 1 ? h : nu;
   const int64_t stride = ws_limbs(nu, nv, hcap);
-  k_divmod<RB, Q, F, TC><<<(unsigned)count, T, (size_t)smem_words * 4, st>>>(
+  int64_t grid = count;
+  if (x.list != nullptr) {  // a listed subset: a few CTAs per SM loop over it
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+      BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t slots = (int64_t)sms * (TC ? 1 : 2);
+    if (grid > slots) grid = slots;
+  }
+  k_divmod<RB, Q, F, TC><<<(unsigned)grid, T, (size_t)smem_words * 4, st>>>(
       u, v, q, r, status, nu, nv, nq, mode, h, reinterpret_cast<uint64_t *>(ws), stride,
-      smem_words, x.w, x.nw, x.v_stride < 0 ? nv : x.v_stride, x.w_stride);
+      smem_words, x.w, x.nw, x.v_stride < 0 ? nv : x.v_stride, x.w_stride, x.list, x.nlist);
   return bigint_launch_status();
 }
 
@@ -259,11 +284,35 @@ static int launch_div_common(const uint64_t *u, const uint64_t *v, uint64_t *q, 
                                                 ws, st, x);
 }
 
-int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
-                  int32_t *status, int64_t count, int nu, int nv, void *ws, size_t,
-                  cudaStream_t st) {
+bool divmod_steps_ok(int64_t count, int nu, int nv, size_t ws_bytes);
+bool divmod_steps_default(int nu, int nv);
+int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                        int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
+                        void *list_and_counters, cudaStream_t st);
+
+// One CTA per division for the listed instances (or all, list = null).
+int launch_divmod_cta(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                      int32_t *status, int64_t count, int nu, int nv, void *ws,
+                      const int32_t *list, const int *nlist, cudaStream_t st) {
   const int nq = nu - nv + 1 > 1 ? nu - nv + 1 : 1;
-  return launch_div_common(u, v, q, r, status, count, nu, nv, nq, 0, nu, ws, st);
+  DivExtra x;
+  x.list = list;
+  x.nlist = nlist;
+  return launch_div_common(u, v, q, r, status, count, nu, nv, nq, 0, nu, ws, st, x);
+}
+
+// The step-batched form (divstep.cu) where it applies, else one CTA per
+// division.
+int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                  int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
+                  cudaStream_t st) {
+  const size_t regions = cta_regions_bytes(count, nu, nv);
+  const bool steps = g_div_steps == 2 ? true : (g_div_steps == 0 && divmod_steps_default(nu, nv));
+  if (steps && ws_bytes >= divmod_workspace(count, nu, nv) &&
+      divmod_steps_ok(count, nu, nv, regions))
+    return launch_divmod_steps(u, v, q, r, status, count, nu, nv, ws, regions,
+                               static_cast<char *>(ws) + regions, st);
+  return launch_divmod_cta(u, v, q, r, status, count, nu, nv, ws, nullptr, nullptr, st);
 }
 
 // q, r of u / v from w = floor(B^h / v) (h >= nu, h >= nv), per instance or

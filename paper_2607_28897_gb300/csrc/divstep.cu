@@ -1,0 +1,306 @@
+// divstep.cu -- division of a uniform batch with every step batched across
+// the instances (Sec. V-C, Fig. 6).
+//
+// The one-CTA-per-division kernel (divmod.cu) runs the whole algorithm of a
+// division on one SM, as the paper's intragroup kernel does.  Its products
+// are as fast as the SM allows, but the Newton loop is sequential: the early
+// steps are tiny, every linear step waits at block barriers, and a batch
+// smaller than a few waves of SMs leaves most of the GPU idle.  Here the
+// division is instead cut at its steps, and each step runs for ALL instances
+// of the batch at once: the products as batched launches of the multiply
+// kernels (tensor-core products from 256 limbs: tcmul.cu, each filling every
+// SM), the linear steps as one small kernel with one CTA per instance.  The
+// arithmetic is that of divmod.cu; only the schedule differs.
+//
+// Every instance of a batch has the same shape (nu, nv), and for the usual
+// operands (top limbs of u and v nonzero, "regular") the same precisions
+// k = nv - 1 and h = nu, so the Newton schedule (l, m, t per step) is known
+// on the host.  Instances whose top limb of u or v is zero (including v = 0)
+// take the one-CTA-per-division kernel in a last launch; the step kernels
+// run over them too (their values are never used, and every size is fixed,
+// so nothing reads out of bounds).
+//
+// Per step, with the iterate w ~ B^(k+l) / v kept to l + 2 limbs,
+// m = min(l - 2, L - l), t = min(k, l + m + 2), vt = top t + 1 limbs of v:
+//   P  = vt w mod B^(t+2)                    (low product, exact)
+//   d  = B^(t+l) - vt w: |d| = P if P < B^(t+2)/2 (d <= 0), else B^(t+2) - P
+//   P2 = w |d|, banded from limb s - 2, s = t + l - m
+//   w' = w B^m + floor(P2 / B^s)             (d >= 0)
+//   w' = w B^m - floor(P2 / B^s) - 1         (d <  0; the ceiling of Fig. 6
+//                                             rounded up by at most one)
+// The band makes floor(P2 / B^s) exact or one unit high; so each step lands
+// within a few units of B^(k+l+m) / v, and since m <= l - 2 the Newton error
+// squared stays below a unit: the error does not grow from step to step.
+// Then q^ = floor(u w / B^h) (banded from limb h - 2), r^ = u - q^ v modulo
+// B^(nv+1), and the exact correction of divmod.cu settles q and r.
+#include "divcore.cuh"
+
+namespace bigint {
+
+using namespace divc;
+
+int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                  int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
+                  cudaStream_t st);
+int launch_divmod_cta(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                      int32_t *status, int64_t count, int nu, int nv, void *ws,
+                      const int32_t *list, const int *nlist, cudaStream_t st);
+size_t divmod_workspace(int64_t count, int nu, int nv);
+
+namespace dstep {
+
+constexpr int LIN_THREADS = 256;  // CTA of the linear per-instance kernels
+
+__device__ __forceinline__ bool regular(const uint64_t *u, int nu, const uint64_t *v, int nv) {
+  return v[nv - 1] != 0 && u[nu - 1] != 0;
+}
+
+// One thread per instance: lists the irregular instances and writes the
+// Newton start w = floor(B^(2 l) / V), V = floor(v / B^(k-l)) + 1, into the
+// first l + 2 limbs of the instance's iterate record (zero for irregular
+// ones, whose divisor may have a zero top limb).
+__global__ void k_ds_start(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, int nu,
+                           int nv, int l, uint64_t *W, int64_t sw, int64_t count,
+                           int32_t *irregular, int *nirr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint64_t *u = U + i * nu, *v = V + i * nv;
+  uint64_t *w = W + i * sw;
+  if (!regular(u, nu, v, nv)) {
+    irregular[atomicAdd(nirr, 1)] = (int32_t)i;
+    for (int j = 0; j < l + 2; j++) w[j] = 0;
+    return;
+  }
+  const int k = nv - 1;
+  uint64_t Vt[6] = {0, 0, 0, 0, 0, 0}, Un[8] = {0, 0, 0, 0, 0, 0, 0, 0}, Qt[8];
+  for (int j = 0; j <= l; j++) Vt[j] = v[k - l + j];
+  int j = 0;
+  while (j <= l && ++Vt[j] == 0) j++;  // V + 1, which may carry into limb l + 1
+  const int nV = j > l ? l + 2 : l + 1;
+  if (j > l) Vt[l + 1] = 1;
+  Un[2 * l] = 1;  // B^(2 l)
+  small_div(Un, 2 * l + 1, Vt, nV, Qt);
+  const int nq = 2 * l + 1 - nV + 1;
+  for (int jj = 0; jj < l + 2; jj++) w[jj] = jj < nq ? Qt[jj] : 0;
+}
+
+// One CTA per instance: the sign of d from P = vt w mod B^nl and |d| (nl
+// limbs): P itself if its top bit is clear (d <= 0), else B^nl - P.
+__global__ void __launch_bounds__(LIN_THREADS)
+    k_ds_mid(const uint64_t *__restrict__ P, int64_t sp, uint64_t *__restrict__ D, int64_t sd,
+             int nl, int32_t *neg) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  const int64_t i = blockIdx.x;
+  const uint64_t *p = P + i * sp;
+  uint64_t *d = D + i * sd;
+  const bool ng = (p[nl - 1] >> 63) == 0;
+  auto store = [&](int j, uint64_t x) { d[j] = x; };
+  if (ng) {
+    for (int j = threadIdx.x; j < nl; j += blockDim.x) d[j] = p[j];
+  } else {
+    auto load = [&](int j) { return make_ulonglong2(0ull, p[j]); };
+    blk_addsub<true>(nl, 0u, load, store, scr);
+  }
+  if (threadIdx.x == 0) neg[i] = ng ? 1 : 0;
+}
+
+// One CTA per instance: w' = w B^m + Y (d >= 0) or w B^m - Y - 1 (d < 0),
+// Y = floor(P2 / B^s) (ny limbs), into nout limbs of the next iterate record.
+__global__ void __launch_bounds__(LIN_THREADS)
+    k_ds_update(const uint64_t *__restrict__ W, int64_t sw, int nw, const uint64_t *__restrict__ Z,
+                int64_t sz, int s, int ny, const int32_t *__restrict__ neg, int m,
+                uint64_t *__restrict__ Wn, int nout) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  const int64_t i = blockIdx.x;
+  const uint64_t *w = W + i * sw, *y = Z + i * sz + s;
+  uint64_t *wn = Wn + i * sw;
+  auto load = [&](int j) {
+    const uint64_t x = (j >= m && j - m < nw) ? w[j - m] : 0ull;
+    return make_ulonglong2(x, j < ny ? y[j] : 0ull);
+  };
+  auto store = [&](int j, uint64_t x) { wn[j] = x; };
+  if (neg[i]) blk_addsub<true>(nout, 1u, load, store, scr);
+  else blk_addsub<false>(nout, 0u, load, store, scr);
+}
+
+// One CTA per instance: q^ = Z[h .. h + nqh) into its record (zero above).
+__global__ void __launch_bounds__(LIN_THREADS)
+    k_ds_tail_q(const uint64_t *__restrict__ Z, int64_t sz, int h, int nqh, uint64_t *Qh,
+                int64_t sq, int nqcap) {
+  const int64_t i = blockIdx.x;
+  const uint64_t *z = Z + i * sz + h;
+  uint64_t *qh = Qh + i * sq;
+  for (int j = threadIdx.x; j < nqcap; j += blockDim.x) qh[j] = j < nqh ? z[j] : 0ull;
+}
+
+// One CTA per regular instance: r^ = (u - R) mod B^(nv+1) with R the low
+// nv + 1 limbs of q^ v, the exact correction of q^ and r^ (divmod.cu), and
+// the results.  Irregular instances are left to the one-CTA-per-division
+// kernel.  A tensor-core product of this division that gave up at a wait
+// limit (*aborted) voids the results: BIGINT_ETIMEOUT.
+__global__ void __launch_bounds__(LIN_THREADS)
+    k_ds_finish(const uint64_t *__restrict__ U, int nu, const uint64_t *__restrict__ V, int nv,
+                const uint64_t *__restrict__ R, int64_t sp, uint64_t *Rh, int64_t sd, uint64_t *Qh,
+                int64_t sq, int nqcap, uint64_t *Qo, int nq, uint64_t *Ro, int32_t *status,
+                const int *aborted) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  const int64_t i = blockIdx.x;
+  const uint64_t *u = U + i * nu, *v = V + i * nv, *rr = R + i * sp;
+  if (!regular(u, nu, v, nv)) return;
+  uint64_t *rh = Rh + i * sd, *qh = Qh + i * sq;
+  {
+    auto load = [&](int j) { return make_ulonglong2(j < nu ? u[j] : 0ull, rr[j]); };
+    auto store = [&](int j, uint64_t x) { rh[j] = x; };
+    blk_addsub<true>(nv + 1, 0u, load, store, scr);
+  }
+  int st = correct(v, nv, rh, qh, nqcap, scr);
+  __syncthreads();
+  const int pq = blk_prec(qh, nqcap, scr);
+  if (pq > nq && st == BIGINT_OK) st = BIGINT_ERANGE;
+  if (*(volatile const int *)aborted) st = BIGINT_ETIMEOUT;
+  uint64_t *q = Qo + i * nq, *r = Ro + i * nv;
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) q[j] = j < nqcap ? qh[j] : 0ull;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) r[j] = rh[j];
+  if (status != nullptr && threadIdx.x == 0) status[i] = st;
+}
+
+// The Newton schedule of a regular instance: (l, m, t) per step.
+struct Step {
+  int l, m, t;
+};
+
+int schedule(int k, int h, int l0, Step *steps, int cap) {
+  const int L = h - k;
+  int l = l0, n = 0;
+  while (l < L && n < cap) {
+    const int m = (l - 2 < L - l) ? l - 2 : L - l;
+    const int t = (k < l + m + 2) ? k : l + m + 2;
+    steps[n++] = Step{l, m, t};
+    l += m;
+  }
+  return n;
+}
+
+// Per-instance record widths (limbs) and the workspace layout.
+struct Layout {
+  int64_t sw, sp, sd, sz, sq;  // iterate, low product, |d| / r^, banded product, q^
+  size_t w0, w1, p, d, z, qh, neg, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+Layout layout(int64_t count, int nu, int nv) {
+  Layout Y;
+  const int L = nu - nv + 1;
+  Y.sw = L + 4;
+  Y.sp = nv + 2;
+  Y.sd = nv + 2;
+  Y.sz = nu + L + 4;
+  Y.sq = L + 4;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  Y.w0 = take(8 * count * Y.sw);
+  Y.w1 = take(8 * count * Y.sw);
+  Y.p = take(8 * count * Y.sp);
+  Y.d = take(8 * count * Y.sd);
+  Y.z = take(8 * count * Y.sz);
+  Y.qh = take(8 * count * Y.sq);
+  Y.neg = take(4 * count);
+  Y.total = o;
+  return Y;
+}
+
+}  // namespace dstep
+
+// Smallest divisor (limbs) for which a uniform batch takes the step-batched
+// form by default; smaller divisions stay in one CTA each.
+constexpr int DIV_STEP_MIN = 128;
+
+// True if divmod_steps can run this shape (with enough workspace).
+bool divmod_steps_ok(int64_t count, int nu, int nv, size_t ws_bytes) {
+  if (count < 1 || nv < 8 || nu < nv) return false;
+  return dstep::layout(count, nu, nv).total <= ws_bytes;
+}
+
+bool divmod_steps_default(int nu, int nv) { return nv >= DIV_STEP_MIN && nu >= nv; }
+
+// q = floor(u / v), r = u - q v for a uniform batch, step by step across the
+// batch (see the top of this file); irregular instances by the
+// one-CTA-per-division kernel at the end.
+// ws: ws_bytes for the step records (the one-CTA-per-division kernel's
+// per-instance regions, reused); list_and_counters: 4 count bytes rounded to
+// 256, then two ints, OUTSIDE those regions (that kernel reads the list
+// while it writes its regions).
+int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                        int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
+                        void *list_and_counters, cudaStream_t st) {
+  using namespace dstep;
+  if (!divmod_steps_ok(count, nu, nv, ws_bytes)) return BIGINT_EINVAL;
+  const Layout Y = layout(count, nu, nv);
+  char *base = static_cast<char *>(ws);
+  uint64_t *W[2] = {reinterpret_cast<uint64_t *>(base + Y.w0),
+                    reinterpret_cast<uint64_t *>(base + Y.w1)};
+  uint64_t *P = reinterpret_cast<uint64_t *>(base + Y.p);
+  uint64_t *D = reinterpret_cast<uint64_t *>(base + Y.d);
+  uint64_t *Z = reinterpret_cast<uint64_t *>(base + Y.z);
+  uint64_t *Qh = reinterpret_cast<uint64_t *>(base + Y.qh);
+  int32_t *neg = reinterpret_cast<int32_t *>(base + Y.neg);
+  int32_t *list = static_cast<int32_t *>(list_and_counters);
+  // [0] irregular instances listed, [1] a tensor-core product gave up
+  int *ctr = reinterpret_cast<int *>(static_cast<char *>(list_and_counters) +
+                                     ((size_t)4 * count + 255) / 256 * 256);
+  const int k = nv - 1, h = nu, L = h - k;
+  const int l0 = L < 3 ? L : 3;
+  const int nq = nu - nv + 1;
+  BIGINT_CUDA_TRY(cudaMemsetAsync(ctr, 0, 8, st));
+  const unsigned g1 = (unsigned)((count + 127) / 128);
+  k_ds_start<<<g1, 128, 0, st>>>(u, v, nu, nv, l0, W[0], Y.sw, count, list, ctr);
+  int rc = bigint_launch_status();
+  if (rc != BIGINT_OK) return rc;
+  Step steps[64];
+  const int ns = schedule(k, h, l0, steps, 64);
+  int cur = 0;
+  for (int i = 0; i < ns; i++) {
+    const Step S = steps[i];
+    const int nw = S.l + 2, nl = S.t + 2;
+    // P = vt w mod B^(t+2)
+    rc = launch_mul_ex(v + (k - S.t), nv, W[cur], Y.sw, P, Y.sp, count, S.t + 1, nw, nl, 0,
+                       ctr + 1, st);
+    if (rc != BIGINT_OK) return rc;
+    k_ds_mid<<<(unsigned)count, LIN_THREADS, 0, st>>>(P, Y.sp, D, Y.sd, nl, neg);
+    if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
+    // P2 = w |d|, its limbs from s on
+    const int s = S.t + S.l - S.m, n2 = nw + nl;
+    rc = launch_mul_ex(W[cur], Y.sw, D, Y.sd, Z, Y.sz, count, nw, nl, n2, s - 2, ctr + 1, st);
+    if (rc != BIGINT_OK) return rc;
+    k_ds_update<<<(unsigned)count, LIN_THREADS, 0, st>>>(W[cur], Y.sw, nw, Z, Y.sz, s, n2 - s,
+                                                         neg, S.m, W[cur ^ 1], S.l + S.m + 2);
+    if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
+    cur ^= 1;
+  }
+  // q^ = floor(u w / B^h), w of L + 2 limbs
+  const int nw = L + 2, nz = nu + nw, nqh = nz - h, nqcap = nqh + 1;
+  rc = launch_mul_ex(u, nu, W[cur], Y.sw, Z, Y.sz, count, nu, nw, nz, h - 2, ctr + 1, st);
+  if (rc != BIGINT_OK) return rc;
+  k_ds_tail_q<<<(unsigned)count, LIN_THREADS, 0, st>>>(Z, Y.sz, h, nqh, Qh, Y.sq, nqcap);
+  if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
+  // R = q^ v mod B^(nv+1)
+  rc = launch_mul_ex(Qh, Y.sq, v, nv, P, Y.sp, count, nqh, nv, nv + 1, 0, ctr + 1, st);
+  if (rc != BIGINT_OK) return rc;
+  k_ds_finish<<<(unsigned)count, LIN_THREADS, 0, st>>>(u, nu, v, nv, P, Y.sp, D, Y.sd, Qh, Y.sq,
+                                                       nqcap, q, nq, r, status, ctr + 1);
+  if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
+  // the irregular instances, one CTA per division (the workspace is free
+  // again: everything above is stream-ordered before this launch)
+  return launch_divmod_cta(u, v, q, r, status, count, nu, nv, ws, list, ctr, st);
+}
+
+size_t divmod_steps_workspace(int64_t count, int nu, int nv) {
+  return dstep::layout(count, nu, nv).total;
+}
+
+}  // namespace bigint

@@ -9,14 +9,15 @@
 
 namespace bigint {
 
+// Instance i: a at A + i sa, b at Bm + i sb, result at Out + i so (limbs).
 template <int RB, int Q, int F, bool ASM, bool PP>
 __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
     k_mul(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
-          uint64_t *__restrict__ Out, int na, int nb, int nout) {
+          uint64_t *__restrict__ Out, int na, int nb, int nout, int64_t sa, int64_t sb,
+          int64_t so) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int64_t inst = blockIdx.x;
-  blk_mul<RB, Q, F, ASM, PP>(A + inst * (int64_t)na, na, Bm + inst * (int64_t)nb, nb,
-                    Out + inst * (int64_t)nout, nout, smem);
+  blk_mul<RB, Q, F, ASM, PP>(A + inst * sa, na, Bm + inst * sb, nb, Out + inst * so, nout, smem);
 }
 
 template <int RB, int Q, int F>
@@ -55,7 +56,8 @@ static int smem_optin() {
 
 template <int RB, int Q, int F, bool ASM = false, bool PP = false>
 static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
-                          int na, int nb, int nout, cudaStream_t st) {
+                          int na, int nb, int nout, cudaStream_t st, int64_t sa = -1,
+                          int64_t sb = -1, int64_t so = -1) {
   const size_t smem = sizeof(uint32_t) * (size_t)blk_mul_smem_words<RB, Q>(na, nb);
   const int optin = smem_optin();
   if (optin == 0) return BIGINT_ECUDA;
@@ -71,7 +73,8 @@ static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, i
   }
   if (smem > (size_t)dyn_max) return BIGINT_EINVAL;
   const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 640 : 1024);
-  k_mul<RB, Q, F, ASM, PP><<<(unsigned)count, T, smem, st>>>(a, b, out, na, nb, nout);
+  k_mul<RB, Q, F, ASM, PP><<<(unsigned)count, T, smem, st>>>(
+      a, b, out, na, nb, nout, sa < 0 ? na : sa, sb < 0 ? nb : sb, so < 0 ? nout : so);
   return bigint_launch_status();
 }
 
@@ -169,6 +172,32 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
     case 9: return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout, st);
     default: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
   }
+}
+
+int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                     int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
+                     cudaStream_t st);
+
+// The low nout limbs of a batch of products whose instances lie at strides
+// sa, sb, so (limbs) -- operands and results inside larger per-instance
+// records, as the step-batched division keeps them.  The tensor-core
+// product runs where launch_mul would pick it (band start lo: limbs >= lo + 2
+// are floor(a b / B^j) or one unit more, see tc_product); other shapes run
+// the integer product exactly (lo ignored: exact is within the band's
+// bound).  abort_flag: set if a tensor-core CTA gave up at a wait limit.
+int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                  int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
+                  cudaStream_t st) {
+  if (count == 0) return BIGINT_OK;
+  const int nmin = na < nb ? na : nb;
+  if (g_mul_variant == 0 || g_mul_variant == 12) {
+    if (nmin >= TC_MIN_LIMBS && mul_tc_smem(na, nb) > 0)
+      return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st);
+  }
+  const int nmax = na > nb ? na : nb;
+  if (nmax < 1536) return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout,
+                                                                 st, sa, sb, so);
+  return launch_variant<29, 16, 32, false, true>(a, b, out, count, na, nb, nout, st, sa, sb, so);
 }
 
 }  // namespace bigint

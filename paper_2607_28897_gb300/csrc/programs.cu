@@ -198,17 +198,8 @@ int launch_poly_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int
 
 // BIGINT_ETIMEOUT if a Poly launch's tensor-core product hit a wait limit
 // since the last call (synchronises the device), else BIGINT_OK.
-int programs_take_timeout() {
-  BIGINT_CUDA_TRY(cudaDeviceSynchronize());
-  int v = 0;
-  BIGINT_CUDA_TRY(cudaMemcpyFromSymbol(&v, tcm::g_timeout, sizeof(int)));
-  if (v) {
-    const int zero = 0;
-    BIGINT_CUDA_TRY(cudaMemcpyToSymbol(tcm::g_timeout, &zero, sizeof(int)));
-    return BIGINT_ETIMEOUT;
-  }
-  return BIGINT_OK;
-}
+int programs_take_timeout() { return tcm::take_timeout_here(); }
+int programs_set_wait_limit(long long cycles) { return tcm::set_wait_limit_here(cycles); }
 
 size_t poly_workspace(int64_t count, int n) {
   int sms = 0;

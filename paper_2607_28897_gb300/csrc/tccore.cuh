@@ -89,8 +89,23 @@ constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles, about one second
 // 24-28 = M >> 4); N >> 3 goes to bits 17-22.
 constexpr uint32_t IDESC_M128 = (1u << 4) | ((uint32_t)(128 >> 4) << 24);
 
-// Set when a CTA gives up at a wait limit (one copy per translation unit).
+// Set when a CTA gives up at a wait limit (one copy per translation unit;
+// each unit that launches tensor-core products reads and clears its own
+// copy through take_timeout_here, and bigint_check_timeout asks them all).
 static __device__ int g_timeout = 0;
+// Cycle limit of the waits of a product (one copy per translation unit, set
+// through set_wait_limit_here; the default is WAIT_LIMIT).  Lowering it
+// makes ordinary products give up, which is how the timeout path is tested;
+// the waits of tc_release always use the full WAIT_LIMIT, so tensor memory
+// is never freed while an MMA that was committed may still write to it.
+static __device__ long long g_wait_limit = WAIT_LIMIT;
+// A flag nothing sets: with a negative g_wait_limit every wait of a product
+// first waits (full limit) for its phase, so no MMA it guards is left in
+// flight, and then runs out on this flag after -g_wait_limit cycles -- a
+// timeout made on purpose, so that tests can drive the timeout path (a
+// positive limit cannot: the phases a product waits for have completed by
+// the time its first probe returns).
+static __device__ int g_never_set = 0;
 
 struct Layout {
   int mx;    // x blocks of 128 digits (8 nx digits, + the carry digit if XC)
@@ -165,12 +180,42 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the phase with this parity to complete; false after WAIT_LIMIT
-// cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Non-blocking probe of the phase with this parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with this parity to complete; false after `limit`
+// cycles (default: the launch's g_wait_limit).  try_wait suspends the
+// thread in hardware for a while before it reports failure, longer than a
+// small product takes, so a lowered limit (the test of the timeout path)
+// polls with the non-blocking test_wait instead, which sees the limit pass.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
+  if (limit < WAIT_LIMIT) {
+    while (!mbar_test_wait(mbar, parity))
+      if (clock64() - t0 > limit) return false;
+    return true;
+  }
   while (!mbar_try_wait(mbar, parity))
-    if (clock64() - t0 > WAIT_LIMIT) return false;
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long lim = *(volatile long long *)&g_wait_limit;
+  if (lim >= 0) return mbar_wait(mbar, parity, lim);
+  if (!mbar_wait(mbar, parity, WAIT_LIMIT)) return false;
+  const long long t0 = clock64();
+  while (*(volatile int *)&g_never_set == 0)
+    if (clock64() - t0 > -lim) return false;
   return true;
 }
 
@@ -469,8 +514,11 @@ __device__ void tc_init(TcCtx &c, uint8_t *sm, TcShared *sh, uint32_t *scr) {
 template <int NT>
 __device__ void tc_release(TcCtx &c) {
   if (c.aborted) {
-    if (c.pending & 1u) mbar_wait(smem_u32(&c.sh->bars[0]), c.phase & 1u);
-    if (c.pending & 2u) mbar_wait(smem_u32(&c.sh->bars[1]), (c.phase >> 1) & 1u);
+    // groups whose commit this thread has not seen arrive (including one
+    // whose wait gave up) may still be running: wait for them with the full
+    // limit before the tensor memory is freed
+    if (c.pending & 1u) mbar_wait(smem_u32(&c.sh->bars[0]), c.phase & 1u, WAIT_LIMIT);
+    if (c.pending & 2u) mbar_wait(smem_u32(&c.sh->bars[1]), (c.phase >> 1) & 1u, WAIT_LIMIT);
     if (threadIdx.x == 0) atomicExch(&g_timeout, 1);
   }
   tc_fence_before();
@@ -577,9 +625,12 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
         }
         if (gi >= 1) {  // group gi-1 used the other buffers
           const int ob = b ^ 1;
-          if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) bad = true;
-          c.phase ^= 1u << ob;
-          c.pending &= ~(1u << ob);
+          if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) {
+            bad = true;  // still pending: tc_release waits for it
+          } else {
+            c.phase ^= 1u << ob;
+            c.pending &= ~(1u << ob);
+          }
           tc_fence_after();
           int slo, shi;
           group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
@@ -591,9 +642,12 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
         if (__syncthreads_or(bad)) { c.aborted = true; return false; }
       }
       const int lb = (NG - 1) & 1;
-      if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) bad = true;  // all: TMEM reuse below
-      c.phase ^= 1u << lb;
-      c.pending &= ~(1u << lb);
+      if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) {  // all: TMEM reuse below
+        bad = true;  // still pending: tc_release waits for it
+      } else {
+        c.phase ^= 1u << lb;
+        c.pending &= ~(1u << lb);
+      }
       tc_fence_after();
       {
         int slo, shi;
@@ -686,6 +740,32 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   }
   __syncthreads();
   return true;
+}
+
+// ---- host side, per translation unit ---------------------------------------
+// BIGINT_ETIMEOUT if a product launched from this translation unit gave up
+// at a wait limit since the last call (synchronises the device; clears the
+// record), else BIGINT_OK.
+static inline int take_timeout_here() {
+  if (cudaDeviceSynchronize() != cudaSuccess) return BIGINT_ECUDA;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_timeout, sizeof(int)) != cudaSuccess) return BIGINT_ECUDA;
+  if (v) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_timeout, &zero, sizeof(int)) != cudaSuccess) return BIGINT_ECUDA;
+    return BIGINT_ETIMEOUT;
+  }
+  return BIGINT_OK;
+}
+
+// Sets the wait limit of the products launched from this translation unit
+// from now on (synchronous): cycles > 0 the limit, 0 the default WAIT_LIMIT,
+// cycles < 0 the injected timeout of g_never_set after -cycles cycles.
+static inline int set_wait_limit_here(long long cycles) {
+  const long long v = cycles != 0 ? cycles : WAIT_LIMIT;
+  if (cudaDeviceSynchronize() != cudaSuccess) return BIGINT_ECUDA;
+  return cudaMemcpyToSymbol(g_wait_limit, &v, sizeof(v)) == cudaSuccess ? BIGINT_OK
+                                                                        : BIGINT_ECUDA;
 }
 
 }  // namespace tcm

@@ -21,10 +21,15 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
 }
 
 // 2 NT drain threads plus one issuer warp (tc_product<NT, G, true, XC>).
+// Instance i's operands start at X + i sx and Y + i sy, its result at
+// Out + i so (limbs); lo > 0 is tc_product's band mode.  A CTA that gives up
+// at a wait limit also sets *abort_flag (if given), so that a caller
+// chaining products (the step-batched division) can report it per instance.
 template <int NT, int G, bool XC>
 __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
-             uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count) {
+             uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count, int64_t sx,
+             int64_t sy, int64_t so, int lo, int *abort_flag) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ TcShared sh;
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
@@ -33,13 +38,14 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
   for (int64_t inst = blockIdx.x; inst < count; inst += gridDim.x) {
     const int64_t next = inst + gridDim.x;
     if (threadIdx.x == 0 && next < count) {
-      prefetch_l2(X + next * (int64_t)nx, 8 * (size_t)nx);
-      prefetch_l2(Y + next * (int64_t)ny, 8 * (size_t)ny);
+      prefetch_l2(X + next * sx, 8 * (size_t)nx);
+      prefetch_l2(Y + next * sy, 8 * (size_t)ny);
     }
-    if (!tc_product<NT, G, true, XC>(c, X + inst * (int64_t)nx, nx, Y + inst * (int64_t)ny, ny,
-                                     Out + inst * (int64_t)nout, nout, 0))
+    if (!tc_product<NT, G, true, XC>(c, X + inst * sx, nx, Y + inst * sy, ny, Out + inst * so,
+                                     nout, lo))
       break;
   }
+  if (c.aborted && abort_flag != nullptr && threadIdx.x == 0) atomicExch(abort_flag, 1);
   tc_release<NT>(c);
 }
 
@@ -152,7 +158,7 @@ static size_t tc_smem(int nx, int ny) {
 // needs, or 0 if it does not fit (or the shapes are out of range).
 size_t mul_tc_smem(int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
-  if (nx < 1 || ny > 16383) return 0;
+  if (nx < 1 || nx > 16383 || ny > 32768) return 0;
   switch (tc_shape(nx, ny)) {
     case TC_64_XC: return tc_smem<64, 7, true>(nx, ny);
     case TC_64_NOXC: return tc_smem<64, 7, false>(nx, ny);
@@ -165,49 +171,79 @@ size_t mul_tc_smem(int na, int nb) {
   }
 }
 
+// Operands and results of one batched product launch: instance i's x at
+// x + i sx, y at y + i sy, result at out + i so (limbs); band start lo (0:
+// the low nout limbs exactly); abort_flag as for k_mul_tc (may be null).
+struct TcArgs {
+  const uint64_t *x, *y;
+  uint64_t *out;
+  int64_t sx, sy, so;
+  int lo;
+  int *abort_flag;
+};
+
 template <int NT, int G, bool XC>
-static int launch_tc(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_t count, int nx,
-                     int ny, int nout, cudaStream_t st) {
+static int launch_tc(const TcArgs &A, int64_t count, int nx, int ny, int nout, cudaStream_t st) {
   const size_t smem = tc_smem<NT, G, XC>(nx, ny);
   if (smem == 0) return BIGINT_EINVAL;
   if (count == 0) return BIGINT_OK;
-  int dev = 0, sms = 0;
-  BIGINT_CUDA_TRY(cudaGetDevice(&dev));
-  BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // device and kernel attributes, read once (a division issues dozens of
+  // these launches back to back)
+  static int sms = 0, smem_sm = 0, reserved = 0, static_smem = 0;
+  if (sms == 0) {
+    int dev = 0, n = 0;
+    BIGINT_CUDA_TRY(cudaGetDevice(&dev));
+    BIGINT_CUDA_TRY(
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    BIGINT_CUDA_TRY(
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    cudaFuncAttributes fa;
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>));
+    static_smem = (int)fa.sharedSizeBytes;
+    BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    sms = n;
+  }
   // CTAs resident at once on an SM: TMEM allows 256 / NT, shared memory
   // per SM / (dynamic + static + the per-block reservation)
-  int smem_sm = 0, reserved = 0;
-  BIGINT_CUDA_TRY(
-      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  BIGINT_CUDA_TRY(
-      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-  cudaFuncAttributes fa;
-  BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>));
-  int per_sm = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+  int per_sm = smem_sm / (int)(smem + static_smem + reserved);
   if (per_sm > 256 / NT) per_sm = 256 / NT;
   if (per_sm < 1) per_sm = 1;
   const int64_t slots = (int64_t)sms * per_sm;
   const int64_t grid = count < slots ? count : slots;
-  tcm::k_mul_tc<NT, G, XC><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(x, y, out, nx, ny, nout,
-                                                                     count);
+  tcm::k_mul_tc<NT, G, XC><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(
+      A.x, A.y, A.out, nx, ny, nout, count, A.sx, A.sy, A.so, A.lo, A.abort_flag);
   return bigint_launch_status();
+}
+
+// Products with strides and a band start (see TcArgs); the shorter operand
+// becomes x.  The column sums stay below 2^31 while the shorter operand has
+// at most 16383 limbs (a column has at most 8 nx + 1 digit products); the
+// longer one only sets how many Toeplitz blocks there are.
+int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                     int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
+                     cudaStream_t st) {
+  TcArgs A{a, b, out, sa, sb, so, lo, abort_flag};
+  int nx = na, ny = nb;
+  if (nb < na) {
+    A.x = b; A.y = a; A.sx = sb; A.sy = sa;
+    nx = nb; ny = na;
+  }
+  if (nx < 1 || nx > 16383 || ny > 32768 || nout < 1 || nout > na + nb || lo < 0 || lo >= nout)
+    return BIGINT_EINVAL;
+  switch (tc_shape(nx, ny)) {
+    case TC_64_XC: return launch_tc<64, 7, true>(A, count, nx, ny, nout, st);
+    case TC_64_NOXC: return launch_tc<64, 7, false>(A, count, nx, ny, nout, st);
+    case TC_128_XC: return launch_tc<128, 8, true>(A, count, nx, ny, nout, st);
+    case TC_128_NOXC: return launch_tc<128, 8, false>(A, count, nx, ny, nout, st);
+    default:
+      return tc_smem<256, 8, true>(nx, ny) ? launch_tc<256, 8, true>(A, count, nx, ny, nout, st)
+                                           : launch_tc<256, 4, true>(A, count, nx, ny, nout, st);
+  }
 }
 
 int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                   int nb, int nout, cudaStream_t st) {
-  const uint64_t *x = a, *y = b;
-  int nx = na, ny = nb;
-  if (nb < na) { x = b; y = a; nx = nb; ny = na; }
-  if (nx < 1 || ny > 16383 || nout < 1 || nout > na + nb) return BIGINT_EINVAL;
-  switch (tc_shape(nx, ny)) {
-    case TC_64_XC: return launch_tc<64, 7, true>(x, y, out, count, nx, ny, nout, st);
-    case TC_64_NOXC: return launch_tc<64, 7, false>(x, y, out, count, nx, ny, nout, st);
-    case TC_128_XC: return launch_tc<128, 8, true>(x, y, out, count, nx, ny, nout, st);
-    case TC_128_NOXC: return launch_tc<128, 8, false>(x, y, out, count, nx, ny, nout, st);
-    default:
-      return tc_smem<256, 8, true>(nx, ny) ? launch_tc<256, 8, true>(x, y, out, count, nx, ny, nout, st)
-                                           : launch_tc<256, 4, true>(x, y, out, count, nx, ny, nout, st);
-  }
+  return launch_mul_tc_ex(a, na, b, nb, out, nout, count, na, nb, nout, 0, nullptr, st);
 }
 
 // ---- split products ----------------------------------------------------------
@@ -303,16 +339,7 @@ int launch_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_
 
 // BIGINT_ETIMEOUT if a tensor-core product hit a wait limit since the last
 // call (synchronises the device), else BIGINT_OK.
-int tc_take_timeout() {
-  BIGINT_CUDA_TRY(cudaDeviceSynchronize());
-  int v = 0;
-  BIGINT_CUDA_TRY(cudaMemcpyFromSymbol(&v, tcm::g_timeout, sizeof(int)));
-  if (v) {
-    const int zero = 0;
-    BIGINT_CUDA_TRY(cudaMemcpyToSymbol(tcm::g_timeout, &zero, sizeof(int)));
-    return BIGINT_ETIMEOUT;
-  }
-  return BIGINT_OK;
-}
+int tc_take_timeout() { return tcm::take_timeout_here(); }
+int tc_set_wait_limit(long long cycles) { return tcm::set_wait_limit_here(cycles); }
 
 }  // namespace bigint
