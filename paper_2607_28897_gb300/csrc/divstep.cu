@@ -41,7 +41,7 @@ using namespace divc;
 
 int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                   int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                  cudaStream_t st);
+                  cudaStream_t st, int tc_min);
 int launch_divmod_cta(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                       int32_t *status, int64_t count, int nu, int nv, void *ws,
                       const int32_t *list, const int *nlist, cudaStream_t st);
@@ -50,6 +50,12 @@ size_t divmod_workspace(int64_t count, int nu, int nv);
 namespace dstep {
 
 constexpr int LIN_THREADS = 256;  // CTA of the linear per-instance kernels
+// Shorter operand (limbs) from which a step's product runs on the tensor
+// cores.  The steps' products are rectangular and come in batches of
+// thousands; measured on 2n/n divisions at n = 512 the 132 x 262-limb and
+// 68 x 134-limb products of the middle steps took 173 and 90 us on the
+// integer pipes for 4096 instances.
+constexpr int STEP_TC_MIN = 64;
 
 __device__ __forceinline__ bool regular(const uint64_t *u, int nu, const uint64_t *v, int nv) {
   return v[nv - 1] != 0 && u[nu - 1] != 0;
@@ -58,7 +64,10 @@ __device__ __forceinline__ bool regular(const uint64_t *u, int nu, const uint64_
 // One thread per instance: lists the irregular instances and writes the
 // Newton start w = floor(B^(2 l) / V), V = floor(v / B^(k-l)) + 1, into the
 // first l + 2 limbs of the instance's iterate record (zero for irregular
-// ones, whose divisor may have a zero top limb).
+// ones, whose divisor may have a zero top limb).  (Running the first,
+// tiny Newton steps in this kernel too, one CTA per instance, was measured
+// slower than their batched launches: 579 us for 4096 instances of 512
+// limbs, the long chains of block barriers of the one-CTA form again.)
 __global__ void k_ds_start(const uint64_t *__restrict__ U, const uint64_t *__restrict__ V, int nu,
                            int nv, int l, uint64_t *W, int64_t sw, int64_t count,
                            int32_t *irregular, int *nirr) {
@@ -84,11 +93,78 @@ __global__ void k_ds_start(const uint64_t *__restrict__ U, const uint64_t *__res
   for (int jj = 0; jj < l + 2; jj++) w[jj] = jj < nq ? Qt[jj] : 0;
 }
 
-// One CTA per instance: the sign of d from P = vt w mod B^nl and |d| (nl
+// ---------------------------------------------------------------------------
+// Per-instance linear steps with one warp per instance: r = x +- y (+- cin)
+// over n limbs in rounds of 32, the carry of each round from two ballots
+// (the scan of Fig. 3, as blk_addsub does across a CTA).  Every lane of the
+// warp calls it.
+// ---------------------------------------------------------------------------
+template <bool SUB, class Load, class Store>
+__device__ __forceinline__ void warp_addsub(int n, uint32_t cin, Load load, Store store) {
+  const uint32_t lane = lane_id();
+  uint32_t c = cin;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + (int)lane;
+    uint32_t g = 0, pr = 1;
+    uint64_t t = 0;
+    if (j < n) {
+      const ulonglong2 xy = load(j);
+      t = SUB ? xy.x - xy.y : xy.x + xy.y;
+      g = SUB ? (xy.x < xy.y) : (t < xy.x);
+      pr = SUB ? (t == 0) : (t == ~0ull);
+    }
+    const uint64_t cm = warp_carries(warp_gp(g, pr), c);
+    const uint32_t cl = (uint32_t)(cm >> lane) & 1u;
+    if (j < n) store(j, SUB ? t - cl : t + cl);
+    c = (uint32_t)(cm >> 32) & 1u;
+  }
+}
+
+constexpr int WARP_CTA = 256;  // warp-per-instance kernels: 8 instances per CTA
+
+// One warp per instance: the sign of d from P = vt w mod B^nl and |d| (nl
 // limbs): P itself if its top bit is clear (d <= 0), else B^nl - P.
-__global__ void __launch_bounds__(LIN_THREADS)
+__global__ void __launch_bounds__(WARP_CTA)
     k_ds_mid(const uint64_t *__restrict__ P, int64_t sp, uint64_t *__restrict__ D, int64_t sd,
-             int nl, int32_t *neg) {
+             int nl, int32_t *neg, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * (WARP_CTA / 32) + (threadIdx.x >> 5);
+  if (i >= count) return;
+  const uint64_t *p = P + i * sp;
+  uint64_t *d = D + i * sd;
+  const bool ng = (p[nl - 1] >> 63) == 0;
+  if (ng) {
+    for (int j = lane_id(); j < nl; j += 32) d[j] = p[j];
+  } else {
+    warp_addsub<true>(nl, 0u, [&](int j) { return make_ulonglong2(0ull, p[j]); },
+                      [&](int j, uint64_t x) { d[j] = x; });
+  }
+  if (lane_id() == 0) neg[i] = ng ? 1 : 0;
+}
+
+// One warp per instance: w' = w B^m + Y (d >= 0) or w B^m - Y - 1 (d < 0),
+// Y = floor(P2 / B^s) (ny limbs), into nout limbs of the next iterate record.
+__global__ void __launch_bounds__(WARP_CTA)
+    k_ds_update(const uint64_t *__restrict__ W, int64_t sw, int nw, const uint64_t *__restrict__ Z,
+                int64_t sz, int s, int ny, const int32_t *__restrict__ neg, int m,
+                uint64_t *__restrict__ Wn, int nout, int64_t count) {
+  const int64_t i = (int64_t)blockIdx.x * (WARP_CTA / 32) + (threadIdx.x >> 5);
+  if (i >= count) return;
+  const uint64_t *w = W + i * sw, *y = Z + i * sz + s;
+  uint64_t *wn = Wn + i * sw;
+  auto load = [&](int j) {
+    const uint64_t x = (j >= m && j - m < nw) ? w[j - m] : 0ull;
+    return make_ulonglong2(x, j < ny ? y[j] : 0ull);
+  };
+  auto store = [&](int j, uint64_t x) { wn[j] = x; };
+  if (neg[i]) warp_addsub<true>(nout, 1u, load, store);
+  else warp_addsub<false>(nout, 0u, load, store);
+}
+
+// The same two steps with one CTA per instance, for wide records (a warp
+// takes its limbs 32 at a time, one round after the other).
+__global__ void __launch_bounds__(LIN_THREADS)
+    k_ds_mid_cta(const uint64_t *__restrict__ P, int64_t sp, uint64_t *__restrict__ D, int64_t sd,
+                 int nl, int32_t *neg) {
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   const int64_t i = blockIdx.x;
   const uint64_t *p = P + i * sp;
@@ -104,12 +180,10 @@ __global__ void __launch_bounds__(LIN_THREADS)
   if (threadIdx.x == 0) neg[i] = ng ? 1 : 0;
 }
 
-// One CTA per instance: w' = w B^m + Y (d >= 0) or w B^m - Y - 1 (d < 0),
-// Y = floor(P2 / B^s) (ny limbs), into nout limbs of the next iterate record.
 __global__ void __launch_bounds__(LIN_THREADS)
-    k_ds_update(const uint64_t *__restrict__ W, int64_t sw, int nw, const uint64_t *__restrict__ Z,
-                int64_t sz, int s, int ny, const int32_t *__restrict__ neg, int m,
-                uint64_t *__restrict__ Wn, int nout) {
+    k_ds_update_cta(const uint64_t *__restrict__ W, int64_t sw, int nw,
+                    const uint64_t *__restrict__ Z, int64_t sz, int s, int ny,
+                    const int32_t *__restrict__ neg, int m, uint64_t *__restrict__ Wn, int nout) {
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   const int64_t i = blockIdx.x;
   const uint64_t *w = W + i * sw, *y = Z + i * sz + s;
@@ -122,6 +196,9 @@ __global__ void __launch_bounds__(LIN_THREADS)
   if (neg[i]) blk_addsub<true>(nout, 1u, load, store, scr);
   else blk_addsub<false>(nout, 0u, load, store, scr);
 }
+
+// Records up to this many limbs take the warp-per-instance kernels.
+constexpr int WARP_LIMBS = 1024;
 
 // One CTA per instance: q^ = Z[h .. h + nqh) into its record (zero above).
 __global__ void __launch_bounds__(LIN_THREADS)
@@ -256,40 +333,48 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
   const int k = nv - 1, h = nu, L = h - k;
   const int l0 = L < 3 ? L : 3;
   const int nq = nu - nv + 1;
-  BIGINT_CUDA_TRY(cudaMemsetAsync(ctr, 0, 8, st));
-  const unsigned g1 = (unsigned)((count + 127) / 128);
-  k_ds_start<<<g1, 128, 0, st>>>(u, v, nu, nv, l0, W[0], Y.sw, count, list, ctr);
-  int rc = bigint_launch_status();
-  if (rc != BIGINT_OK) return rc;
   Step steps[64];
   const int ns = schedule(k, h, l0, steps, 64);
+  BIGINT_CUDA_TRY(cudaMemsetAsync(ctr, 0, 8, st));
+  k_ds_start<<<(unsigned)((count + 127) / 128), 128, 0, st>>>(u, v, nu, nv, l0, W[0], Y.sw, count,
+                                                              list, ctr);
+  int rc = bigint_launch_status();
+  if (rc != BIGINT_OK) return rc;
   int cur = 0;
+  const unsigned gw = (unsigned)((count + WARP_CTA / 32 - 1) / (WARP_CTA / 32));
   for (int i = 0; i < ns; i++) {
     const Step S = steps[i];
     const int nw = S.l + 2, nl = S.t + 2;
     // P = vt w mod B^(t+2)
     rc = launch_mul_ex(v + (k - S.t), nv, W[cur], Y.sw, P, Y.sp, count, S.t + 1, nw, nl, 0,
-                       ctr + 1, st);
+                       ctr + 1, st, STEP_TC_MIN);
     if (rc != BIGINT_OK) return rc;
-    k_ds_mid<<<(unsigned)count, LIN_THREADS, 0, st>>>(P, Y.sp, D, Y.sd, nl, neg);
+    if (nl <= WARP_LIMBS)
+      k_ds_mid<<<gw, WARP_CTA, 0, st>>>(P, Y.sp, D, Y.sd, nl, neg, count);
+    else
+      k_ds_mid_cta<<<(unsigned)count, LIN_THREADS, 0, st>>>(P, Y.sp, D, Y.sd, nl, neg);
     if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
     // P2 = w |d|, its limbs from s on
     const int s = S.t + S.l - S.m, n2 = nw + nl;
-    rc = launch_mul_ex(W[cur], Y.sw, D, Y.sd, Z, Y.sz, count, nw, nl, n2, s - 2, ctr + 1, st);
+    rc = launch_mul_ex(W[cur], Y.sw, D, Y.sd, Z, Y.sz, count, nw, nl, n2, s - 2, ctr + 1, st, STEP_TC_MIN);
     if (rc != BIGINT_OK) return rc;
-    k_ds_update<<<(unsigned)count, LIN_THREADS, 0, st>>>(W[cur], Y.sw, nw, Z, Y.sz, s, n2 - s,
-                                                         neg, S.m, W[cur ^ 1], S.l + S.m + 2);
+    if (S.l + S.m + 2 <= WARP_LIMBS)
+      k_ds_update<<<gw, WARP_CTA, 0, st>>>(W[cur], Y.sw, nw, Z, Y.sz, s, n2 - s, neg, S.m,
+                                           W[cur ^ 1], S.l + S.m + 2, count);
+    else
+      k_ds_update_cta<<<(unsigned)count, LIN_THREADS, 0, st>>>(
+          W[cur], Y.sw, nw, Z, Y.sz, s, n2 - s, neg, S.m, W[cur ^ 1], S.l + S.m + 2);
     if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
     cur ^= 1;
   }
   // q^ = floor(u w / B^h), w of L + 2 limbs
   const int nw = L + 2, nz = nu + nw, nqh = nz - h, nqcap = nqh + 1;
-  rc = launch_mul_ex(u, nu, W[cur], Y.sw, Z, Y.sz, count, nu, nw, nz, h - 2, ctr + 1, st);
+  rc = launch_mul_ex(u, nu, W[cur], Y.sw, Z, Y.sz, count, nu, nw, nz, h - 2, ctr + 1, st, STEP_TC_MIN);
   if (rc != BIGINT_OK) return rc;
   k_ds_tail_q<<<(unsigned)count, LIN_THREADS, 0, st>>>(Z, Y.sz, h, nqh, Qh, Y.sq, nqcap);
   if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
   // R = q^ v mod B^(nv+1)
-  rc = launch_mul_ex(Qh, Y.sq, v, nv, P, Y.sp, count, nqh, nv, nv + 1, 0, ctr + 1, st);
+  rc = launch_mul_ex(Qh, Y.sq, v, nv, P, Y.sp, count, nqh, nv, nv + 1, 0, ctr + 1, st, STEP_TC_MIN);
   if (rc != BIGINT_OK) return rc;
   k_ds_finish<<<(unsigned)count, LIN_THREADS, 0, st>>>(u, nu, v, nv, P, Y.sp, D, Y.sd, Qh, Y.sq,
                                                        nqcap, q, nq, r, status, ctr + 1);

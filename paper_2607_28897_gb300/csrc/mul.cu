@@ -185,13 +185,14 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
 // are floor(a b / B^j) or one unit more, see tc_product); other shapes run
 // the integer product exactly (lo ignored: exact is within the band's
 // bound).  abort_flag: set if a tensor-core CTA gave up at a wait limit.
+// tc_min: shorter operand (limbs) from which the tensor cores are used.
 int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                   int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                  cudaStream_t st) {
+                  cudaStream_t st, int tc_min) {
   if (count == 0) return BIGINT_OK;
   const int nmin = na < nb ? na : nb;
   if (g_mul_variant == 0 || g_mul_variant == 12) {
-    if (nmin >= TC_MIN_LIMBS && mul_tc_smem(na, nb) > 0)
+    if (nmin >= tc_min && mul_tc_smem(na, nb) > 0)
       return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st);
   }
   const int nmax = na > nb ? na : nb;

@@ -147,6 +147,23 @@ static TcShape tc_shape(int nx, int ny) {
   return TC_256;
 }
 
+// The same choice for the columns a product actually computes: the low nout
+// limbs (nout < nx + ny) and, in band mode, only the columns from the one
+// that holds limb lo (tc_product's tiles start there).  A low or banded
+// product often needs far fewer columns than the full one, and the smaller
+// tile then runs several CTAs per SM.
+static TcShape tc_shape_cols(int nx, int ny, int nout, int lo) {
+  const int ey = (8 * ny + 127) / 128;
+  const int need = (nout + 15) / 16, first = lo > 0 ? lo / 16 : 0;
+  auto width = [&](int mx) { return (mx + ey < need ? mx + ey : need) - first; };
+  const int wx = width((8 * nx + 1 + 127) / 128), w0 = width((8 * nx + 127) / 128);
+  if (wx <= 64) return TC_64_XC;
+  if (w0 <= 64) return TC_64_NOXC;
+  if (wx <= 128) return TC_128_XC;
+  if (w0 <= 128) return TC_128_NOXC;
+  return TC_256;
+}
+
 template <int NT, int G, bool XC>
 static size_t tc_smem(int nx, int ny) {
   const tcm::Layout L = tcm::layout<NT, G, XC>(nx, ny);
@@ -219,6 +236,30 @@ static int launch_tc(const TcArgs &A, int64_t count, int nx, int ny, int nout, c
 // becomes x.  The column sums stay below 2^31 while the shorter operand has
 // at most 16383 limbs (a column has at most 8 nx + 1 digit products); the
 // longer one only sets how many Toeplitz blocks there are.
+// Toeplitz blocks (each eight MMAs) the tiles of a product with x of nx and
+// y of ny limbs issue, following tc_product's tile loop: for each tile the
+// blocks e whose columns meet x.
+static long tc_blocks(int nx, int ny, int nout, int lo, int NT, bool XC) {
+  const int mx = (8 * nx + (XC ? 1 : 0) + 127) / 128, ey = (8 * ny + 127) / 128;
+  const int ctot = mx + ey, cfirst = lo > 0 ? lo / 16 : 0;
+  long blocks = 0;
+  for (int c0 = cfirst; 16 * c0 < nout; c0 += NT) {
+    int W = ctot - c0;
+    if (W > NT) W = NT;
+    const int need = (nout - 16 * c0 + 15) / 16;
+    if (W > need) W = need;
+    W = (W + 15) & ~15;
+    if (16 * (c0 + W) <= lo) continue;
+    const int e_lo = c0 - mx + 1 > 0 ? c0 - mx + 1 : 0;
+    const int e_hi = c0 + W - 1 < ey ? c0 + W - 1 : ey;
+    if (e_hi >= e_lo) blocks += e_hi - e_lo + 1;
+  }
+  return blocks;
+}
+
+static int tc_nt(TcShape sh) { return sh == TC_256 ? 256 : (sh >= TC_128_XC ? 128 : 64); }
+static bool tc_xc(TcShape sh) { return sh == TC_64_XC || sh == TC_128_XC || sh == TC_256; }
+
 int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                      int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
                      cudaStream_t st) {
@@ -230,7 +271,34 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
   }
   if (nx < 1 || nx > 16383 || ny > 32768 || nout < 1 || nout > na + nb || lo < 0 || lo >= nout)
     return BIGINT_EINVAL;
-  switch (tc_shape(nx, ny)) {
+  // x is the operand stored whole in shared memory (the B side), y the one
+  // whose Toeplitz blocks are the A side.  While an MMA is narrower than
+  // ~136 columns its time is its A operand's read, so a product issues
+  // fewer MMAs, each wider, with the SHORTER operand as y when that lowers
+  // the blocks issued (a low product whose longer operand has most of the
+  // columns); the longer operand then has to fit shared memory as x.
+  TcShape sh = tc_shape_cols(nx, ny, nout, lo);
+  if (nx != ny && ny <= 16383) {
+    const TcShape sw = tc_shape_cols(ny, nx, nout, lo);
+    const long keep = tc_blocks(nx, ny, nout, lo, tc_nt(sh), tc_xc(sh));
+    const long swap = tc_blocks(ny, nx, nout, lo, tc_nt(sw), tc_xc(sw));
+    if (tc_nt(sw) < 256 && swap < keep) {
+      size_t need = 0;
+      switch (sw) {
+        case TC_64_XC: need = tc_smem<64, 7, true>(ny, nx); break;
+        case TC_64_NOXC: need = tc_smem<64, 7, false>(ny, nx); break;
+        case TC_128_XC: need = tc_smem<128, 8, true>(ny, nx); break;
+        default: need = tc_smem<128, 8, false>(ny, nx); break;
+      }
+      if (need > 0) {
+        const uint64_t *tp = A.x; A.x = A.y; A.y = tp;
+        const int64_t ts = A.sx; A.sx = A.sy; A.sy = ts;
+        const int tn = nx; nx = ny; ny = tn;
+        sh = sw;
+      }
+    }
+  }
+  switch (sh) {
     case TC_64_XC: return launch_tc<64, 7, true>(A, count, nx, ny, nout, st);
     case TC_64_NOXC: return launch_tc<64, 7, false>(A, count, nx, ny, nout, st);
     case TC_128_XC: return launch_tc<128, 8, true>(A, count, nx, ny, nout, st);
