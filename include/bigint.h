@@ -98,19 +98,22 @@ int bigint_mul_lo(const uint64_t *a, const uint64_t *b, uint64_t *out,
                   int64_t count, int32_t na, int32_t nb, int32_t m,
                   void *stream);
 
-/* The products of bigint_mul, with each product's output tiles (4096 limbs
- * of the result each) computed by different CTAs and then linked by a
- * second, small kernel (the carries between tiles and the column-sum bias
- * are settled there): for few, large products (serving) the latency falls
- * by up to the number of tiles.  Products that run on the 256-column
- * tensor-core tile with more than one tile (na + nb > 4096 and the smaller
- * operand small enough for the tile's shared memory, about 10000 limbs)
- * split; any other product runs as bigint_mul.
- * Results are bit-identical to bigint_mul.
+/* The products of bigint_mul with each product spread over several CTAs,
+ * for few, large products (serving), where one CTA per product would leave
+ * most SMs idle.  Up to 16 products with a shorter operand of 256 limbs or
+ * more: each product's output tiles (4096 limbs each) are cut further into
+ * units of consecutive groups of Toeplitz blocks, about one unit per SM;
+ * every unit adds its tile's partial column sums into a buffer in the
+ * workspace with integer atomic adds (exact, in any order), and one CTA per
+ * product turns the sums into limbs.  Larger batches: each product's output
+ * tiles on different CTAs, linked by a second small kernel (the carries
+ * between tiles and the column-sum bias are settled there).  Any other
+ * product runs as bigint_mul.  Results are bit-identical to bigint_mul.
  * workspace: bigint_mul_split_workspace(count, na, nb) bytes of device
- * memory (16 bytes per tile; 0 when nothing splits), 8-byte aligned;
- * BIGINT_ENOMEM if smaller.  Multi-CTA per instance: a latency form, not
- * part of Sec. VI's one-instance-per-CTA design.                           */
+ * memory (up to 512 KB per product for the column sums of the first form,
+ * 16 bytes per tile for the second, 0 when nothing splits), 8-byte
+ * aligned; BIGINT_ENOMEM if smaller.  Multi-CTA per instance: a latency
+ * form, not part of Sec. VI's one-instance-per-CTA design.                 */
 size_t bigint_mul_split_workspace(int64_t count, int32_t na, int32_t nb);
 int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out,
                      int64_t count, int32_t na, int32_t nb, void *workspace,

@@ -192,8 +192,15 @@ static size_t cta_regions_bytes(int64_t count, int nu, int nv) {
   return (size_t)count * (size_t)ws_limbs(nu, nv, nu) * sizeof(uint64_t);
 }
 
-size_t divmod_workspace(int64_t count, int nu, int nv) {
+size_t divmod_sk_bytes(int64_t count, int nu, int nv);
+
+// ... and, for a small batch, the column sums of its split-K products.
+static size_t list_end(int64_t count, int nu, int nv) {
   return cta_regions_bytes(count, nu, nv) + ((size_t)4 * count + 255) / 256 * 256 + 256;
+}
+
+size_t divmod_workspace(int64_t count, int nu, int nv) {
+  return list_end(count, nu, nv) + divmod_sk_bytes(count, nu, nv);
 }
 
 size_t shinv_workspace(int64_t count, int nv, int h) {
@@ -288,7 +295,7 @@ bool divmod_steps_ok(int64_t count, int nu, int nv, size_t ws_bytes);
 bool divmod_steps_default(int nu, int nv);
 int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                         int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
-                        void *list_and_counters, cudaStream_t st);
+                        void *list_and_counters, void *sk, size_t sk_bytes, cudaStream_t st);
 
 // One CTA per division for the listed instances (or all, list = null).
 int launch_divmod_cta(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
@@ -309,9 +316,12 @@ int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r
   const size_t regions = cta_regions_bytes(count, nu, nv);
   const bool steps = g_div_steps == 2 ? true : (g_div_steps == 0 && divmod_steps_default(nu, nv));
   if (steps && ws_bytes >= divmod_workspace(count, nu, nv) &&
-      divmod_steps_ok(count, nu, nv, regions))
-    return launch_divmod_steps(u, v, q, r, status, count, nu, nv, ws, regions,
-                               static_cast<char *>(ws) + regions, st);
+      divmod_steps_ok(count, nu, nv, regions)) {
+    const size_t skb = divmod_sk_bytes(count, nu, nv);
+    char *w = static_cast<char *>(ws);
+    return launch_divmod_steps(u, v, q, r, status, count, nu, nv, ws, regions, w + regions,
+                               skb ? w + list_end(count, nu, nv) : nullptr, skb, st);
+  }
   return launch_divmod_cta(u, v, q, r, status, count, nu, nv, ws, nullptr, nullptr, st);
 }
 

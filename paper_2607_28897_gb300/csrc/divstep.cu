@@ -41,7 +41,7 @@ using namespace divc;
 
 int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                   int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                  cudaStream_t st, int tc_min);
+                  cudaStream_t st, int tc_min, void *sk_ws, size_t sk_bytes);
 int launch_divmod_cta(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                       int32_t *status, int64_t count, int nu, int nv, void *ws,
                       const int32_t *list, const int *nlist, cudaStream_t st);
@@ -311,10 +311,11 @@ bool divmod_steps_default(int nu, int nv) { return nv >= DIV_STEP_MIN && nu >= n
 // ws: ws_bytes for the step records (the one-CTA-per-division kernel's
 // per-instance regions, reused); list_and_counters: 4 count bytes rounded to
 // 256, then two ints, OUTSIDE those regions (that kernel reads the list
-// while it writes its regions).
+// while it writes its regions); sk: sk_bytes for the column sums of the
+// split-K products of a small batch (null: none).
 int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
                         int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
-                        void *list_and_counters, cudaStream_t st) {
+                        void *list_and_counters, void *sk, size_t sk_bytes, cudaStream_t st) {
   using namespace dstep;
   if (!divmod_steps_ok(count, nu, nv, ws_bytes)) return BIGINT_EINVAL;
   const Layout Y = layout(count, nu, nv);
@@ -347,7 +348,7 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
     const int nw = S.l + 2, nl = S.t + 2;
     // P = vt w mod B^(t+2)
     rc = launch_mul_ex(v + (k - S.t), nv, W[cur], Y.sw, P, Y.sp, count, S.t + 1, nw, nl, 0,
-                       ctr + 1, st, STEP_TC_MIN);
+                       ctr + 1, st, STEP_TC_MIN, sk, sk_bytes);
     if (rc != BIGINT_OK) return rc;
     if (nl <= WARP_LIMBS)
       k_ds_mid<<<gw, WARP_CTA, 0, st>>>(P, Y.sp, D, Y.sd, nl, neg, count);
@@ -356,7 +357,7 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
     if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
     // P2 = w |d|, its limbs from s on
     const int s = S.t + S.l - S.m, n2 = nw + nl;
-    rc = launch_mul_ex(W[cur], Y.sw, D, Y.sd, Z, Y.sz, count, nw, nl, n2, s - 2, ctr + 1, st, STEP_TC_MIN);
+    rc = launch_mul_ex(W[cur], Y.sw, D, Y.sd, Z, Y.sz, count, nw, nl, n2, s - 2, ctr + 1, st, STEP_TC_MIN, sk, sk_bytes);
     if (rc != BIGINT_OK) return rc;
     if (S.l + S.m + 2 <= WARP_LIMBS)
       k_ds_update<<<gw, WARP_CTA, 0, st>>>(W[cur], Y.sw, nw, Z, Y.sz, s, n2 - s, neg, S.m,
@@ -369,12 +370,12 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
   }
   // q^ = floor(u w / B^h), w of L + 2 limbs
   const int nw = L + 2, nz = nu + nw, nqh = nz - h, nqcap = nqh + 1;
-  rc = launch_mul_ex(u, nu, W[cur], Y.sw, Z, Y.sz, count, nu, nw, nz, h - 2, ctr + 1, st, STEP_TC_MIN);
+  rc = launch_mul_ex(u, nu, W[cur], Y.sw, Z, Y.sz, count, nu, nw, nz, h - 2, ctr + 1, st, STEP_TC_MIN, sk, sk_bytes);
   if (rc != BIGINT_OK) return rc;
   k_ds_tail_q<<<(unsigned)count, LIN_THREADS, 0, st>>>(Z, Y.sz, h, nqh, Qh, Y.sq, nqcap);
   if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
   // R = q^ v mod B^(nv+1)
-  rc = launch_mul_ex(Qh, Y.sq, v, nv, P, Y.sp, count, nqh, nv, nv + 1, 0, ctr + 1, st, STEP_TC_MIN);
+  rc = launch_mul_ex(Qh, Y.sq, v, nv, P, Y.sp, count, nqh, nv, nv + 1, 0, ctr + 1, st, STEP_TC_MIN, sk, sk_bytes);
   if (rc != BIGINT_OK) return rc;
   k_ds_finish<<<(unsigned)count, LIN_THREADS, 0, st>>>(u, nu, v, nv, P, Y.sp, D, Y.sd, Qh, Y.sq,
                                                        nqcap, q, nq, r, status, ctr + 1);
@@ -386,6 +387,38 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
 
 size_t divmod_steps_workspace(int64_t count, int nu, int nv) {
   return dstep::layout(count, nu, nv).total;
+}
+
+size_t mul_sk_bytes_per_product(int na, int nb, int nout, int lo);
+
+// Batches of at most this many divisions cut their large products over the
+// SMs (split-K): a handful of divisions would otherwise run each product on
+// a handful of SMs.
+constexpr int64_t DIV_SK_MAX_COUNT = 16;
+
+// Column-sum bytes the split-K products of a batch of count 2n/n-shaped
+// divisions need (0 for larger batches): the largest over the products of
+// the step schedule and of the tail.
+size_t divmod_sk_bytes(int64_t count, int nu, int nv) {
+  if (count < 1 || count > DIV_SK_MAX_COUNT || nu < nv) return 0;
+  const int k = nv - 1, h = nu, L = h - k, l0 = L < 3 ? L : 3;
+  dstep::Step steps[64];
+  const int ns = dstep::schedule(k, h, l0, steps, 64);
+  size_t per = 0;
+  auto take = [&](int na, int nb, int nout, int lo) {
+    const size_t b = mul_sk_bytes_per_product(na, nb, nout, lo);
+    if (b > per) per = b;
+  };
+  for (int i = 0; i < ns; i++) {
+    const dstep::Step S = steps[i];
+    const int nw = S.l + 2, nl = S.t + 2;
+    take(S.t + 1, nw, nl, 0);
+    take(nw, nl, nw + nl, S.t + S.l - S.m - 2);
+  }
+  const int nw = L + 2;
+  take(nu, nw, nu + nw, h - 2);
+  take(nw, nv, nv + 1, 0);
+  return (size_t)count * per;
 }
 
 }  // namespace bigint

@@ -186,14 +186,28 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
 // the integer product exactly (lo ignored: exact is within the band's
 // bound).  abort_flag: set if a tensor-core CTA gave up at a wait limit.
 // tc_min: shorter operand (limbs) from which the tensor cores are used.
+// sk_ws, sk_bytes: room for the column sums of the split-K form, which few
+// large products take (null: never).
+size_t mul_sk_bytes_per_product(int na, int nb, int nout, int lo);
+bool mul_sk_worth(int64_t count, int na, int nb, int nout, int lo);
+int launch_mul_tc_sk(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                     int64_t so, int64_t count, int na, int nb, int nout, int lo, void *colsum,
+                     size_t colsum_bytes, int *abort_flag, cudaStream_t st);
+
 int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                   int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                  cudaStream_t st, int tc_min) {
+                  cudaStream_t st, int tc_min, void *sk_ws, size_t sk_bytes) {
   if (count == 0) return BIGINT_OK;
   const int nmin = na < nb ? na : nb;
   if (g_mul_variant == 0 || g_mul_variant == 12) {
-    if (nmin >= tc_min && mul_tc_smem(na, nb) > 0)
+    if (nmin >= tc_min && mul_tc_smem(na, nb) > 0) {
+      // few products: cut each into units over the SMs (split-K)
+      if (sk_ws != nullptr && mul_sk_worth(count, na, nb, nout, lo) &&
+          sk_bytes >= (size_t)count * mul_sk_bytes_per_product(na, nb, nout, lo))
+        return launch_mul_tc_sk(a, sa, b, sb, out, so, count, na, nb, nout, lo, sk_ws, sk_bytes,
+                                abort_flag, st);
       return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st);
+    }
   }
   const int nmax = na > nb ? na : nb;
   if (nmax < 1536) return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout,

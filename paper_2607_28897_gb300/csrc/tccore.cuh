@@ -742,6 +742,129 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   return true;
 }
 
+// ---- partial tiles (split-K) ---------------------------------------------
+// Groups [g0, g1) of tile `tile` of x * y (x with its carry digit, tiles of
+// NT columns from column cfirst), added into colsum: for each of the tile's
+// columns c (relative to the tile) and positions t, the int32 partial sum of
+// the coefficient 128 (c0 + c) + t is added to colsum[c * 128 + t] with an
+// atomic add (exact and order-independent: a coefficient's full sum is below
+// 2^31 in magnitude, so every partial sum is too).  The CTAs of one product
+// thus share its tiles' Toeplitz blocks, and tc_colsum_limbs turns the sums
+// into limbs.  Returns false (and sets c.aborted) if a wait hit its limit.
+template <int NT, int G>
+__device__ bool tc_partial(TcCtx &c, const uint64_t *x, int nx, const uint64_t *y, int ny,
+                           int c0, int W, int g0, int g1, int *colsum) {
+  constexpr int DRAIN = 2 * NT, THREADS = DRAIN + 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = tid == DRAIN, worker = tid < DRAIN;
+  const Layout Ly = layout<NT, G, true>(nx, ny);
+  uint8_t *sm = c.sm;
+  const uint32_t sbase = c.sbase;
+  const uint32_t xs_a = sbase + Ly.xs, z_a = sbase + Ly.z;
+  const uint32_t lbo_b = (uint32_t)Ly.ptot * 16u;
+  const uint32_t mb[2] = {smem_u32(&c.sh->bars[0]), smem_u32(&c.sh->bars[1])};
+  const int q = warp & 3, cq = warp >> 2;
+  const uint32_t t_lane = c.tmem + ((uint32_t)(32 * q) << 16);
+  const int e_lo = c0 - Ly.mx + 1 > 0 ? c0 - Ly.mx + 1 : 0;
+  const int e_hi = c0 + W - 1 < Ly.ey ? c0 + W - 1 : Ly.ey;
+  const int NG = e_hi >= e_lo ? (e_hi - e_lo + G) / G : 0;
+  if (g1 > NG) g1 = NG;
+  if (g0 >= g1) return true;
+  const int ng = g1 - g0;
+  int acc[64];
+#pragma unroll
+  for (int i = 0; i < 64; i++) acc[i] = 0;
+
+  for (int i = tid; i < ZB * 128 / 16; i += THREADS)
+    reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
+  fill_x<true>(sm + Ly.xs, x, nx, Ly.ptot);
+  auto last_block = [&](int gi) { return e_lo + gi * G + G - 1 < e_hi ? e_lo + gi * G + G - 1 : e_hi; };
+  if (worker) hank_build<G, DRAIN>(sm + Ly.h0, sm + Ly.cs, hank_load<G>(y, ny, last_block(g0), tid), tid);
+  fence_async_smem();
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < ng; k++) {
+    const int gi = g0 + k, b = k & 1;
+    const int ea = e_lo + gi * G, eb = last_block(gi);
+    if (issuer)
+      issue_group(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a, z_a,
+                  lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
+    c.pending |= 1u << b;
+    const bool more = k + 1 < ng && worker;
+    HankLimbs hv{0ull, 0ull};
+    if (more) hv = hank_load<G>(y, ny, last_block(gi + 1), tid);
+    if (k >= 1) {
+      const int ob = b ^ 1;
+      if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) {
+        bad = true;
+      } else {
+        c.phase ^= 1u << ob;
+        c.pending &= ~(1u << ob);
+      }
+      tc_fence_after();
+      int slo, shi;
+      group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
+      if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
+    }
+    if (more) hank_build<G, DRAIN>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
+    tc_fence_before();
+    fence_async_smem();
+    if (__syncthreads_or(bad)) { c.aborted = true; return false; }
+  }
+  const int lb = (ng - 1) & 1;
+  if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) {
+    bad = true;
+  } else {
+    c.phase ^= 1u << lb;
+    c.pending &= ~(1u << lb);
+  }
+  tc_fence_after();
+  {
+    int slo, shi;
+    group_span(c0, W, e_lo + (g1 - 1) * G, last_block(g1 - 1), Ly.mx, slo, shi);
+    if (worker) drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
+  }
+  tc_fence_before();
+  if (__syncthreads_or(bad)) { c.aborted = true; return false; }
+  if (worker) {
+    const int t = 127 - (32 * q + lane);
+#pragma unroll
+    for (int i = 0; i < 64; i++) {
+      const int col = 64 * cq + i;
+      if (col < W && acc[i] != 0) atomicAdd(&colsum[col * 128 + t], acc[i]);
+    }
+  }
+  __syncthreads();  // the shared memory (x, Hankel buffers) is reused by the next unit
+  return true;
+}
+
+// out[L0 .. nout) of the product whose column sums (coefficients 128 c + t
+// for the columns c from cfirst = L0 / 16 on) are in colsum[(c - cfirst) *
+// 128 + t], by the whole CTA: limb j is V_j = sum_k (coef(8 j + k) + 2^31)
+// 2^(8 k), i.e. its low word plus the high word of V_(j-1) (plus `margin` at
+// L0), less the bias sum of the column sums (0x8080808080000000 at L0,
+// 0x8080808080808080 above); one carry scan then one borrow scan
+// (blk_add_then_sub), as at the end of each of tc_product's tiles.
+__device__ inline void tc_colsum_limbs(const int *colsum, int L0, int nout, uint64_t margin,
+                                uint64_t *out, uint32_t *scr) {
+  auto V = [&](int j) {
+    const int *cs = colsum + (size_t)(j - L0) * 8;  // 16 limbs per 128-position column
+    unsigned __int128 v = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v += (unsigned __int128)((uint32_t)cs[k] ^ 0x80000000u) << (8 * k);
+    return v;
+  };
+  auto load = [&](int jj) {
+    const int j = L0 + jj;
+    const uint64_t hi = jj == 0 ? margin : (uint64_t)(V(j - 1) >> 64);
+    return make_ulonglong2((uint64_t)V(j), hi);
+  };
+  auto bias = [&](int jj) { return jj == 0 ? 0x8080808080000000ull : 0x8080808080808080ull; };
+  auto store = [&](int jj, uint64_t v) { out[L0 + jj] = v; };
+  uint32_t cc = 0, bb = 0;
+  blk_add_then_sub(nout - L0, &cc, &bb, load, bias, store, scr);
+}
+
 // ---- host side, per translation unit ---------------------------------------
 // BIGINT_ETIMEOUT if a product launched from this translation unit gave up
 // at a wait limit since the last call (synchronises the device; clears the

@@ -72,6 +72,52 @@ __global__ void __launch_bounds__(2 * NT + 32, 1)
   tc_release<NT>(c);
 }
 
+// ---- split-K products ---------------------------------------------------------
+// A product cut into units of (tile, groups of Toeplitz blocks) so that even
+// a single product keeps many SMs busy (tc_partial adds each unit's column
+// sums into the product's buffer; k_tc_sk_finish turns them into limbs).
+constexpr int SK_MAX_TILES = 8;
+struct SkPlan {
+  int T;                          // tiles
+  int gpc;                        // groups per unit
+  int cfirst;                     // first column of the first tile
+  int c0[SK_MAX_TILES], W[SK_MAX_TILES];
+  int first[SK_MAX_TILES + 1];    // first unit of each tile; first[T] units per product
+};
+
+template <int NT, int G>
+__global__ void __launch_bounds__(2 * NT + 32, 1)
+    k_mul_tc_sk(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y, int nx, int ny,
+                int64_t sx, int64_t sy, int64_t count, SkPlan P, int *colsum, int64_t cs_stride,
+                int *abort_flag) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ TcShared sh;
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  TcCtx c;
+  tc_init<NT>(c, sm, &sh, scr);
+  const int upi = P.first[P.T];
+  for (int64_t u = blockIdx.x; u < count * upi; u += gridDim.x) {
+    const int64_t inst = u / upi;
+    const int r = (int)(u - inst * upi);
+    int t = 0;
+    while (t + 1 < P.T && P.first[t + 1] <= r) t++;
+    const int g0 = (r - P.first[t]) * P.gpc;
+    if (!tc_partial<NT, G>(c, X + inst * sx, nx, Y + inst * sy, ny, P.c0[t], P.W[t], g0,
+                           g0 + P.gpc, colsum + inst * cs_stride + (P.c0[t] - P.cfirst) * 128))
+      break;
+  }
+  if (c.aborted && abort_flag != nullptr && threadIdx.x == 0) atomicExch(abort_flag, 1);
+  tc_release<NT>(c);
+}
+
+// One CTA per product: its limbs [L0, nout) from its column sums.
+__global__ void __launch_bounds__(512)
+    k_tc_sk_finish(const int *colsum, int64_t cs_stride, uint64_t *Out, int64_t so, int L0,
+                   int nout, uint64_t margin) {
+  __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
+  tc_colsum_limbs(colsum + blockIdx.x * cs_stride, L0, nout, margin, Out + blockIdx.x * so, scr);
+}
+
 // One CTA per product: tile t (limbs [t L, t L + L), L = tile_limbs) was
 // computed without what flows in from tile t - 1, i.e. the high word H of
 // that tile's last column sum and its carry out k.  So the product is the
@@ -314,6 +360,151 @@ int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t c
   return launch_mul_tc_ex(a, na, b, nb, out, nout, count, na, nb, nout, 0, nullptr, st);
 }
 
+// ---- split-K products (host) --------------------------------------------------
+namespace {
+
+template <int G>
+int sk_dyn_max() {
+  static int dyn = -1;
+  if (dyn < 0) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc_sk<256, G>) != cudaSuccess) return 0;
+    const int d = optin - (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(tcm::k_mul_tc_sk<256, G>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, d) != cudaSuccess)
+      return 0;
+    dyn = d;
+  }
+  return dyn;
+}
+
+int sm_count_cached() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  }
+  return sms;
+}
+
+// Tiles of 256 columns of the low nout limbs of x * y (x with its carry
+// digit) from the column of limb lo on, as tc_product computes them; groups
+// of G blocks per tile.  Returns false if there are more than SK_MAX_TILES.
+bool sk_tiles(int nx, int ny, int nout, int lo, int G, tcm::SkPlan &P, int *groups) {
+  const int mx = (8 * nx + 1 + 127) / 128, ey = (8 * ny + 127) / 128, ctot = mx + ey;
+  P.cfirst = lo > 0 ? lo / 16 : 0;
+  P.T = 0;
+  for (int c0 = P.cfirst; 16 * c0 < nout; c0 += 256) {
+    if (P.T == tcm::SK_MAX_TILES) return false;
+    int W = ctot - c0;
+    if (W > 256) W = 256;
+    const int need = (nout - 16 * c0 + 15) / 16;
+    if (W > need) W = need;
+    W = (W + 15) & ~15;
+    const int e_lo = c0 - mx + 1 > 0 ? c0 - mx + 1 : 0, e_hi = c0 + W - 1 < ey ? c0 + W - 1 : ey;
+    P.c0[P.T] = c0;
+    P.W[P.T] = W;
+    groups[P.T] = e_hi >= e_lo ? (e_hi - e_lo + G) / G : 0;
+    P.T++;
+  }
+  return P.T > 0;
+}
+
+}  // namespace
+
+// Column-sum buffer bytes of one split-K product (0: not splittable).
+// (Shared memory bound as for the split products: the opt-in limit per block
+// of sm_100 and sm_103 less room for the kernel's static shared memory, so
+// that the size does not depend on querying a device.)
+constexpr size_t SK_SMEM_CAP = 232448 - 2048;
+
+size_t mul_sk_bytes_per_product(int na, int nb, int nout, int lo) {
+  const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
+  tcm::SkPlan P;
+  int groups[tcm::SK_MAX_TILES];
+  if (nx < 1 || nx > 16383 || ny > 32768 || nout < 1 || nout > na + nb || lo < 0 || lo >= nout)
+    return 0;
+  if (tcm::layout<256, 4, true>(nx, ny).total > SK_SMEM_CAP) return 0;
+  if (!sk_tiles(nx, ny, nout, lo, 8, P, groups)) return 0;
+  return (size_t)P.T * 256 * 128 * sizeof(int);
+}
+
+// True if the split-K form would run more units than the ordinary launch
+// has CTAs busy: few products (count x tiles well below the SMs).
+bool mul_sk_worth(int64_t count, int na, int nb, int nout, int lo) {
+  const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
+  if (nx < 256 || mul_sk_bytes_per_product(na, nb, nout, lo) == 0) return false;
+  tcm::SkPlan P;
+  int groups[tcm::SK_MAX_TILES];
+  if (!sk_tiles(nx, ny, nout, lo, 8, P, groups)) return false;
+  const int sms = sm_count_cached();
+  return sms > 0 && count * P.T * 2 <= sms;
+}
+
+// The low nout limbs (from limb lo: band mode, as tc_product) of a batch of
+// products, each cut into units of (tile, groups) spread over the SMs; the
+// units add their column sums into `colsum` (count x
+// mul_sk_bytes_per_product bytes, zeroed here), then one CTA per product
+// forms the limbs.  Results are those of tc_product (bit-identical).
+int launch_mul_tc_sk(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
+                     int64_t so, int64_t count, int na, int nb, int nout, int lo, void *colsum,
+                     size_t colsum_bytes, int *abort_flag, cudaStream_t st) {
+  const uint64_t *x = a, *y = b;
+  int64_t sx = sa, sy = sb;
+  int nx = na, ny = nb;
+  if (nb < na) { x = b; y = a; sx = sb; sy = sa; nx = nb; ny = na; }
+  if (count == 0) return BIGINT_OK;
+  if (nx < 1 || nx > 16383 || ny > 32768 || nout < 1 || nout > na + nb || lo < 0 || lo >= nout)
+    return BIGINT_EINVAL;
+  const size_t per = mul_sk_bytes_per_product(na, nb, nout, lo);
+  if (per == 0 || colsum == nullptr || colsum_bytes < per * (size_t)count) return BIGINT_EINVAL;
+  const int sms = sm_count_cached();
+  if (sms == 0) return BIGINT_ECUDA;
+  int G = 8;
+  size_t smem = tcm::layout<256, 8, true>(nx, ny).total;
+  if (sk_dyn_max<8>() <= 0 || smem > (size_t)sk_dyn_max<8>()) {
+    G = 4;
+    smem = tcm::layout<256, 4, true>(nx, ny).total;
+    if (sk_dyn_max<4>() <= 0 || smem > (size_t)sk_dyn_max<4>()) return BIGINT_EINVAL;
+  }
+  tcm::SkPlan P;
+  int groups[tcm::SK_MAX_TILES];
+  if (!sk_tiles(nx, ny, nout, lo, G, P, groups)) return BIGINT_EINVAL;
+  // groups per unit: about one unit per SM over the whole launch (each unit
+  // first stages x and its first Hankel buffer, so units are not cut finer)
+  int64_t total = 0;
+  for (int t = 0; t < P.T; t++) total += groups[t];
+  total *= count;
+  int64_t gpc = (total + sms - 1) / sms;
+  if (gpc < 1) gpc = 1;
+  P.gpc = (int)gpc;
+  P.first[0] = 0;
+  for (int t = 0; t < P.T; t++) P.first[t + 1] = P.first[t] + (int)((groups[t] + gpc - 1) / gpc);
+  const int64_t units = count * P.first[P.T];
+  BIGINT_CUDA_TRY(cudaMemsetAsync(colsum, 0, per * (size_t)count, st));
+  const int64_t stride = (int64_t)(per / sizeof(int));
+  const unsigned grid = (unsigned)(units < sms ? units : sms);
+  if (G == 8)
+    tcm::k_mul_tc_sk<256, 8><<<grid, 2 * 256 + 32, smem, st>>>(
+        x, y, nx, ny, sx, sy, count, P, static_cast<int *>(colsum), stride, abort_flag);
+  else
+    tcm::k_mul_tc_sk<256, 4><<<grid, 2 * 256 + 32, smem, st>>>(
+        x, y, nx, ny, sx, sy, count, P, static_cast<int *>(colsum), stride, abort_flag);
+  int rc = bigint_launch_status();
+  if (rc != BIGINT_OK) return rc;
+  const int L0 = 16 * P.cfirst;
+  tcm::k_tc_sk_finish<<<(unsigned)count, 512, 0, st>>>(static_cast<const int *>(colsum), stride,
+                                                       out, so, L0, nout,
+                                                       lo > 0 ? (1ull << 32) : 0ull);
+  return bigint_launch_status();
+}
+
 // ---- split products ----------------------------------------------------------
 int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na, int nb,
                int nout, cudaStream_t st);
@@ -378,23 +569,37 @@ int split_tiles(int nx, int ny) {
 
 }  // namespace
 
+// Batches of at most this many products take the split-K form in
+// bigint_mul_split (its column-sum buffers grow with the batch).
+constexpr int64_t SPLIT_SK_MAX_COUNT = 16;
+
 size_t mul_split_workspace(int64_t count, int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
-  return (size_t)16 * (size_t)count * (size_t)split_tiles(nx, ny);
+  const size_t tiles = (size_t)16 * (size_t)count * (size_t)split_tiles(nx, ny);
+  if (count > SPLIT_SK_MAX_COUNT || nx < 256) return tiles;
+  const size_t sk = (size_t)count * mul_sk_bytes_per_product(na, nb, na + nb, 0);
+  return sk > tiles ? sk : tiles;
 }
 
-// The full products of launch_mul with each product's tiles on different
-// CTAs (split_tiles), or launch_mul itself where the product has one tile or
-// another shape.
+// The full products of launch_mul spread over CTAs: up to SPLIT_SK_MAX_COUNT
+// products in the split-K form (units of tile and groups, about one per SM),
+// larger batches with each product's tiles on different CTAs (split_tiles),
+// and launch_mul itself where the product has one tile or another shape.
 int launch_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                      int nb, void *ws, size_t bytes, cudaStream_t st) {
+  const size_t need = count > 0 ? mul_split_workspace(count, na, nb) : 0;
+  if (need == 0) return launch_mul(a, b, out, count, na, nb, na + nb, st);
+  if (bytes < need) return BIGINT_ENOMEM;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % 8) != 0) return BIGINT_EINVAL;
+  // a few products: each cut into (tile, groups) units over the SMs
+  if (count <= SPLIT_SK_MAX_COUNT && mul_sk_worth(count, na, nb, na + nb, 0))
+    return launch_mul_tc_sk(a, na, b, nb, out, na + nb, count, na, nb, na + nb, 0, ws, bytes,
+                            nullptr, st);
   const uint64_t *x = a, *y = b;
   int nx = na, ny = nb;
   if (nb < na) { x = b; y = a; nx = nb; ny = na; }
   const int T = split_tiles(nx, ny);
-  if (T == 0 || count == 0) return launch_mul(a, b, out, count, na, nb, na + nb, st);
-  if (bytes < mul_split_workspace(count, na, nb)) return BIGINT_ENOMEM;
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) % 8) != 0) return BIGINT_EINVAL;
+  if (T == 0) return launch_mul(a, b, out, count, na, nb, na + nb, st);
   uint64_t *tcarry = static_cast<uint64_t *>(ws);
   const size_t s8 = tcm::layout<SPLIT_NT, 8>(nx, ny).total;
   const size_t s4 = tcm::layout<SPLIT_NT, 4>(nx, ny).total;

@@ -26,14 +26,20 @@ def test_addsub_mul_argument_checks(L):
 
 
 def test_mul_split_checks(L):
-    """Workspace: 16 bytes per 4096-limb tile of each split product, none for
-    products that do not split; short or misaligned workspaces are refused."""
+    """Workspace: up to 16 products, the column sums of each 256-column tile
+    (256 x 128 int32) of the split-K form; larger batches, 16 bytes per
+    4096-limb tile of each tile-split product; none for products that do not
+    split; short or misaligned workspaces are refused."""
     import paper_2607_28897_gb300 as bi
 
-    assert L.bigint_mul_split_workspace(2, 4096, 4096) == 16 * 2 * 2
-    assert L.bigint_mul_split_workspace(3, 8192, 8192) == 16 * 3 * 4
-    assert L.bigint_mul_split_workspace(1, 2048, 2049) == 16 * 2
-    assert L.bigint_mul_split_workspace(4, 512, 512) == 0
+    tile_sums = 256 * 128 * 4
+    assert L.bigint_mul_split_workspace(2, 4096, 4096) == 2 * 2 * tile_sums
+    assert L.bigint_mul_split_workspace(3, 8192, 8192) == 3 * 4 * tile_sums
+    assert L.bigint_mul_split_workspace(1, 2048, 2049) == 2 * tile_sums
+    assert L.bigint_mul_split_workspace(4, 512, 512) == 4 * tile_sums
+    assert L.bigint_mul_split_workspace(17, 4096, 4096) == 16 * 17 * 2  # tile split
+    assert L.bigint_mul_split_workspace(17, 512, 512) == 0
+    assert L.bigint_mul_split_workspace(4, 100, 512) == 0  # shorter operand too small
     assert L.bigint_mul_split_workspace(1, 12000, 12000) == 0  # x beyond shared memory
     assert L.bigint_mul_split_workspace(-1, 4096, 4096) == 0
     p = ctypes.c_void_p(256)
@@ -41,7 +47,7 @@ def test_mul_split_checks(L):
     assert L.bigint_mul_split(p, p, p, 1, bi.MUL_MAX_LIMBS + 1, 4, p, 0, None) == bi.EINVAL
     assert L.bigint_mul_split(None, None, None, 0, 4, 4, None, 0, None) == bi.OK
     assert L.bigint_mul_split(p, p, p, 2, 4096, 4096, p, 63, None) == bi.ENOMEM
-    assert L.bigint_mul_split(p, p, p, 2, 4096, 4096, ctypes.c_void_p(260), 64,
+    assert L.bigint_mul_split(p, p, p, 2, 4096, 4096, ctypes.c_void_p(260), 1 << 20,
                               None) == bi.EINVAL
 
 

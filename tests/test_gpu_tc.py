@@ -106,17 +106,25 @@ def test_same_as_integer_variant(bi):
 
 @pytest.mark.parametrize("na,nb,count", [(2048, 2049, 3), (4096, 4096, 2), (3000, 5000, 2),
                                          (1, 8000, 2), (8192, 8192, 2), (10000, 10000, 1),
-                                         (9000, 10000, 1), (2100, 2100, 170)])
+                                         (9000, 10000, 1), (512, 512, 4), (300, 7000, 1),
+                                         (8192, 8192, 16), (2100, 2100, 170),
+                                         (4096, 4096, 17)])
 def test_split(bi, orc, na, nb, count):
-    """Each product's 4096-limb output tiles on different CTAs, linked by the
-    finishing kernel: bit-identical to the oracle and to the one-CTA form
-    (ragged last tiles, a one-limb operand, more units than SMs)."""
+    """Products spread over CTAs -- up to 16 products cut into (tile, groups)
+    units that add their column sums atomically (split-K), larger batches
+    with each 4096-limb output tile on its own CTA, linked by a finishing
+    kernel -- bit-identical to the oracle and to the one-CTA form (ragged
+    last tiles, a one-limb operand, more units than SMs)."""
     from paper_2607_28897_gb300 import inputs
 
     a = inputs.limbs(1200 + na, count, na)
     b = inputs.limbs(1300 + nb, count, nb)
     tiles = -(-(na + nb) // 4096)
-    assert bi.mul_split_workspace_bytes(count, na, nb) == 16 * count * tiles
+    ws = bi.mul_split_workspace_bytes(count, na, nb)
+    if count > 16 or min(na, nb) < 256:
+        assert ws == 16 * count * tiles  # tile split
+    else:
+        assert ws >= count * tiles * 256 * 128 * 4  # column sums of every tile
     da, db = to_dev(a), to_dev(b)
     got = to_host(bi.mul_split(da, db))
     assert np.array_equal(got, orc.batch_mul(a, b))
@@ -139,13 +147,13 @@ def test_split_extreme_digits(bi, orc, pattern):
 
 
 def test_split_small_shapes_run_unsplit(bi, orc):
-    """A product with one tile (or below the 256-column tile) needs no
-    workspace and runs as the ordinary product."""
+    """Larger batches of products with a single tile need no workspace and
+    run as the ordinary product."""
     from paper_2607_28897_gb300 import inputs
 
-    a = inputs.limbs(51, 4, 512)
-    b = inputs.limbs(52, 4, 512)
-    assert bi.mul_split_workspace_bytes(4, 512, 512) == 0
+    a = inputs.limbs(51, 40, 512)
+    b = inputs.limbs(52, 40, 512)
+    assert bi.mul_split_workspace_bytes(40, 512, 512) == 0
     got = to_host(bi.mul_split(to_dev(a), to_dev(b)))
     assert np.array_equal(got, orc.batch_mul(a, b))
 
