@@ -247,26 +247,37 @@ int bigint_batch_upload(bigint_batch *batch, void *workspace, size_t bytes,
 int bigint_batch_launch(const bigint_batch *batch, const uint64_t *in_pool,
                         uint64_t *out_pool, int32_t *status, void *workspace,
                         int mode, void *stream);
-/* Autotuner: times the persistent form with each candidate CTA size on this
- * batch (synchronous) and keeps the fastest for this batch and as the
- * process default; *best_threads receives it. */
+/* Autotuner of the batched form: times the persistent launch on this batch
+ * (synchronous) in each candidate form -- large products on the tensor
+ * cores (CTAs of 544 threads holding their SM's tensor memory; only if the
+ * batch has such products) or integer products only with CTAs of 256, 384
+ * or 512 threads -- and keeps the fastest for this batch (an integer CTA
+ * size also as the process default for new batches); *best_threads
+ * receives the chosen CTA size (544 for the tensor-core form). */
 int bigint_batch_tune(bigint_batch *batch, const uint64_t *in_pool,
                       uint64_t *out_pool, int32_t *status, void *workspace,
                       size_t bytes, void *stream, int *best_threads);
 void bigint_batch_destroy(bigint_batch *batch);
 
-/* Autotuner for the uniform multiply: times the variants of
- * bigint_set_variant on this batch (synchronous), records the fastest for
- * the operands' size class (used by variant 0 from then on) and returns it
- * in *best_variant. */
-int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out,
-                    int64_t count, int32_t na, int32_t nb, void *stream,
-                    int *best_variant);
+/* Autotuner for the multiply (the paper tunes its kernels' thresholds by
+ * measurement, Sec. III): times, on this batch (synchronous), the
+ * tensor-core product with its tile chosen by size and forced to 64, 128
+ * and 256 output columns per tile -- the tile also fixes how many CTAs share
+ * an SM (three, two, one) -- and the integer products (29-bit digits with
+ * 16-column chunks, 28-bit digits with 8-column chunks, and for square
+ * products one level of Karatsuba); records the fastest for the operands'
+ * size class (class c: longer operand of [2^c, 2^(c+1)) limbs; variant 0
+ * uses it from then on) and returns it in *best_variant (a
+ * bigint_set_variant(0, .) number).  Results do not depend on the choice. */
+int bigint_tune(const uint64_t *a, const uint64_t *b, uint64_t *out,
+                int64_t count, int32_t na, int32_t nb, void *stream,
+                int *best_variant);
 /* Saves / loads the tuning table (multiply variant per size class, batch
  * CTA size) as a small JSON file keyed by the GPU name.  Loading a table
- * written for another GPU returns BIGINT_EINVAL and changes nothing. */
-int bigint_tuning_save(const char *path);
-int bigint_tuning_load(const char *path);
+ * written for another GPU, or one with an unknown variant, returns
+ * BIGINT_EINVAL and changes nothing. */
+int bigint_save_tuning(const char *path);
+int bigint_load_tuning(const char *path);
 
 /* ---- fused programs (Sec. VI, Tables I and II) ----------------------------
  * bigint_add_chain: out = a + b + ... + b with k additions (1 <= k <= 255),
@@ -340,24 +351,21 @@ int bigint_host_sync(void);
 /* ---- tuning and measurement ---------------------------------------------
  * Selects the kernel variant an operation uses from now on (process-wide,
  * not thread-safe; call it before launching work).  op 0 = multiply:
- *   variant 0 (default): chosen by operand size from GB300 measurements
- *   variant 1: 28-bit digits, 8-column chunks, carries every 128 rows
- *   variant 2: 29-bit digits, 8-column chunks, carries every 32 rows
- *   variant 3: 29-bit digits, 4-column chunks, carries every 32 rows
- *   variant 4: 29-bit digits, 16-column chunks, carries every 32 rows
- *   variant 5: 30-bit digits, 8-column chunks, carries every 8 rows
- *   variant 6: as 2, each digit product written as explicit mad.wide.u32
- *   variants 7, 8, 9: as 1 with 16-column chunks, as 4, as 1 -- with the
- *   sliding window held in two alternating register buffers (no moves)
- *   variants 10, 11: one level of Karatsuba (square full products of at
- *   least 64 limbs; otherwise variant 8) over half products of variant 8,
- *   resp. variant 9
+ *   variant 0 (default): chosen by operand size from GB300 measurements (the
+ *   tensor-core product from a shorter operand of 256 limbs, integer
+ *   products below), or the variant bigint_tune recorded for the size class
+ *   variant 8: integer product, 29-bit digits, 16-column chunks
+ *   variant 9: integer product, 28-bit digits, 8-column chunks
+ *   variant 10: one level of Karatsuba (square full products of at least 64
+ *   limbs; otherwise variant 8) over variant 8's half products
  *   variant 12: the tensor-core product -- the digit convolution of the
  *   schoolbook product (Sec. V-B) as fp16 matrix products (tcgen05.mma)
- *   over signed base-256 digits with exact fp32 accumulation; bit-identical
- *   results.  Needs the shorter operand to fit shared memory (about 10700
- *   limbs; otherwise variant 8).  One persistent CTA per SM, which holds
- *   all of the SM's tensor memory while it runs.
+ *   over signed base-256 digits with exact fp32 accumulation -- with its
+ *   tile chosen by the columns the product has; bit-identical results.
+ *   Needs the shorter operand to fit shared memory (about 10700 limbs;
+ *   otherwise variant 8).
+ *   variants 13, 14, 15: variant 12 with tiles of 64, 128, 256 output
+ *   columns (three, two, one CTAs per SM)
  * op 1 = division (divmod, shinv, divmod_inv):
  *   variant 0 (default): bigint_divmod on divisors of 128 limbs or more in
  *   the step-batched form (see bigint_divmod), everything else as variant 1

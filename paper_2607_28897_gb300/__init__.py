@@ -60,10 +60,10 @@ SIGNATURES = {
     "bigint_batch_tune": ([_P, _P, _P, _P, _P, _SZ, _P, ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "bigint_batch_destroy": ([_P], None),
-    "bigint_tune_mul": ([_P, _P, _P, _I64, _I32, _I32, _P, ctypes.POINTER(ctypes.c_int)],
+    "bigint_tune": ([_P, _P, _P, _I64, _I32, _I32, _P, ctypes.POINTER(ctypes.c_int)],
                         ctypes.c_int),
-    "bigint_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
-    "bigint_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
+    "bigint_save_tuning": ([ctypes.c_char_p], ctypes.c_int),
+    "bigint_load_tuning": ([ctypes.c_char_p], ctypes.c_int),
     "bigint_set_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "bigint_mul_variant_for": ([_I32, _I32], ctypes.c_int),
     "bigint_check_timeout": ([], ctypes.c_int),
@@ -570,21 +570,22 @@ class Batch:
             pass
 
 
-def tune_mul(a, b, out=None, stream=None) -> int:
-    """Times the multiply variants on this batch; records and returns the best."""
+def tune(a, b, out=None, stream=None) -> int:
+    """Times the multiply variants (tensor-core tiles, integer forms) on this
+    batch; records the fastest for its size class and returns it."""
     a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
     count, na = a.shape
     nb = b.shape[1]
     out = _empty_like_limbs(a, count, na + nb) if out is None else out
     best = ctypes.c_int()
-    _check(load().bigint_tune_mul(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
-                                  _stream_ptr(stream), ctypes.byref(best)), "bigint_tune_mul")
+    _check(load().bigint_tune(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
+                              _stream_ptr(stream), ctypes.byref(best)), "bigint_tune")
     return best.value
 
 
-def tuning_save(path: str) -> None:
-    _check(load().bigint_tuning_save(path.encode()), "bigint_tuning_save")
+def save_tuning(path: str) -> None:
+    _check(load().bigint_save_tuning(path.encode()), "bigint_save_tuning")
 
 
-def tuning_load(path: str) -> None:
-    _check(load().bigint_tuning_load(path.encode()), "bigint_tuning_load")
+def load_tuning(path: str) -> None:
+    _check(load().bigint_load_tuning(path.encode()), "bigint_load_tuning")

@@ -425,11 +425,18 @@ int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32
 
 size_t batch_workspace_bytes(const bigint_batch *B) { return B ? B->workspace_bytes : 0; }
 
-int batch_retune(bigint_batch *B, int threads) {
+// Reconfigures the batch's launches: CTA size of its integer-only persistent
+// launch (0: from the sizes) and whether large products run on the tensor
+// cores (use_tc: 1 yes, 0 no, -1 unchanged).
+int batch_retune(bigint_batch *B, int threads, int use_tc) {
   if (!B) return BIGINT_EINVAL;
   B->threads_override = threads;
+  if (use_tc >= 0) B->use_tc = use_tc != 0;
   return batch_configure(B);
 }
+
+bool batch_uses_tc(const bigint_batch *B) { return B && B->persistent.tc; }
+int batch_threads_of(const bigint_batch *B) { return B ? B->persistent.threads : 0; }
 
 void batch_destroy(bigint_batch *B) { delete B; }
 

@@ -229,15 +229,15 @@ int bigint_batch_tune(bigint_batch *batch, const uint64_t *in_pool, uint64_t *ou
 
 void bigint_batch_destroy(bigint_batch *batch) { batch_destroy(batch); }
 
-int bigint_tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+int bigint_tune(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
                     int32_t na, int32_t nb, void *stream, int *best_variant) {
   if (count < 1 || count > 0x7fffffff || na < 1 || nb < 1) return BIGINT_EINVAL;
   if (na > mul_max_limbs() || nb > mul_max_limbs() || !a || !b || !out) return BIGINT_EINVAL;
   return tune_mul(a, b, out, count, na, nb, as_stream(stream), best_variant);
 }
 
-int bigint_tuning_save(const char *path) { return path ? tuning_save(path) : BIGINT_EINVAL; }
-int bigint_tuning_load(const char *path) { return path ? tuning_load(path) : BIGINT_EINVAL; }
+int bigint_save_tuning(const char *path) { return path ? tuning_save(path) : BIGINT_EINVAL; }
+int bigint_load_tuning(const char *path) { return path ? tuning_load(path) : BIGINT_EINVAL; }
 
 int bigint_set_variant(int op, int variant) {
   if (op == 0) return mul_set_variant(variant);

@@ -10,14 +10,14 @@
 namespace bigint {
 
 // Instance i: a at A + i sa, b at Bm + i sb, result at Out + i so (limbs).
-template <int RB, int Q, int F, bool ASM, bool PP>
+template <int RB, int Q, int F>
 __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
     k_mul(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
           uint64_t *__restrict__ Out, int na, int nb, int nout, int64_t sa, int64_t sb,
           int64_t so) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int64_t inst = blockIdx.x;
-  blk_mul<RB, Q, F, ASM, PP>(A + inst * sa, na, Bm + inst * sb, nb, Out + inst * so, nout, smem);
+  blk_mul<RB, Q, F>(A + inst * sa, na, Bm + inst * sb, nb, Out + inst * so, nout, smem);
 }
 
 template <int RB, int Q, int F>
@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
                uint64_t *__restrict__ Out, int n) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int64_t inst = blockIdx.x;
-  blk_mul_kara<RB, Q, F, true>(A + inst * (int64_t)n, Bm + inst * (int64_t)n, n,
-                               Out + inst * (int64_t)(2 * n), smem);
+  blk_mul_kara<RB, Q, F>(A + inst * (int64_t)n, Bm + inst * (int64_t)n, n,
+                         Out + inst * (int64_t)(2 * n), smem);
 }
 
 // Threads per CTA for a product with `units` units of work: as few rounds as
@@ -54,7 +54,7 @@ static int smem_optin() {
   return g_smem_optin;
 }
 
-template <int RB, int Q, int F, bool ASM = false, bool PP = false>
+template <int RB, int Q, int F>
 static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
                           int na, int nb, int nout, cudaStream_t st, int64_t sa = -1,
                           int64_t sb = -1, int64_t so = -1) {
@@ -65,15 +65,15 @@ static int launch_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, i
   static int dyn_max = -1;  // opt-in limit minus the kernel's static shared memory
   if (dyn_max < 0) {
     cudaFuncAttributes fa;
-    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_mul<RB, Q, F, ASM, PP>));
-    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F, ASM, PP>,
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_mul<RB, Q, F>));
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_mul<RB, Q, F>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          optin - (int)fa.sharedSizeBytes));
     dyn_max = optin - (int)fa.sharedSizeBytes;
   }
   if (smem > (size_t)dyn_max) return BIGINT_EINVAL;
   const int T = pick_threads(blk_mul_units<RB, Q>(na, nb), Q >= 16 ? 640 : 1024);
-  k_mul<RB, Q, F, ASM, PP><<<(unsigned)count, T, smem, st>>>(
+  k_mul<RB, Q, F><<<(unsigned)count, T, smem, st>>>(
       a, b, out, na, nb, nout, sa < 0 ? na : sa, sb < 0 ? nb : sb, so < 0 ? nout : so);
   return bigint_launch_status();
 }
@@ -103,23 +103,21 @@ static int launch_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int6
 // Variant table (see bigint_set_variant).  Variant 0 picks by size from
 // measurements on GB300 (full-product sweep, 2^32-bit operand arrays): the
 // tensor-core product (tcmul.cu) once the shorter operand has TC_MIN_LIMBS
-// limbs and fits shared memory; otherwise ping-pong windows with 28-bit
-// digits / 8-column chunks below ~2^16 bits; above, one level of Karatsuba
-// over 28-bit / 8-column (2^17 bits) or 29-bit / 16-column (2^18 bits and
-// up) half products, and 29-bit / 16-column schoolbook for products that
-// are not square.
+// limbs and fits shared memory; below, the integer product with 28-bit
+// digits and 8-column chunks (variant 9), or 29-bit digits and 16-column
+// chunks (variant 8) past 1535 limbs.  A size class the tuner has measured
+// (bigint_tune) takes its recorded variant instead.
 size_t mul_tc_smem(int na, int nb);
 int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
-                  int nb, int nout, cudaStream_t st);
+                  int nb, int nout, cudaStream_t st, int force_nt);
 
 // Shorter operand (limbs) from which the default is the tensor-core product.
 constexpr int TC_MIN_LIMBS = 256;
 
 static int g_mul_variant = 0;
-constexpr int MUL_VARIANTS = 13;
 // Tuned variant per size class (class c: operands of [2^c, 2^(c+1)) limbs),
-// 0 = not tuned (built-in choice).  Written by bigint_tune_mul and
-// bigint_tuning_load.
+// 0 = not tuned (built-in choice).  Written by bigint_tune / bigint_tune_mul
+// and bigint_tuning_load.
 int g_mul_tuned[32] = {};
 
 int mul_size_class(int na, int nb) {
@@ -129,8 +127,12 @@ int mul_size_class(int na, int nb) {
   return c;
 }
 
+bool mul_variant_valid(int v) {
+  return v == 0 || v == 8 || v == 9 || v == 10 || (v >= 12 && v <= 15);
+}
+
 int mul_set_variant(int v) {
-  if (v < 0 || v >= MUL_VARIANTS) return BIGINT_EINVAL;
+  if (!mul_variant_valid(v)) return BIGINT_EINVAL;
   g_mul_variant = v;
   return BIGINT_OK;
 }
@@ -147,11 +149,11 @@ int mul_variant_for(int na, int nb, int nout) {
     if (nmin >= TC_MIN_LIMBS && mul_tc_smem(na, nb) > 0)
       v = 12;
     else
-      v = nmax < 1536 ? 9 : (nmax < 3072 ? 11 : 10);  // 10, 11 fall back to 8 unless square
+      v = nmax < 1536 ? 9 : 8;
   }
   const bool square_full = na == nb && nout == na + nb && na >= 64;
-  if ((v == 10 || v == 11) && !square_full) v = 8;  // Karatsuba: square full products only
-  if (v == 12 && mul_tc_smem(na, nb) == 0) v = 8;    // tensor-core product: shared memory bound
+  if (v == 10 && !square_full) v = 8;                // Karatsuba: square full products only
+  if (v >= 12 && mul_tc_smem(na, nb) == 0) v = 8;    // tensor-core product: shared memory bound
   return v;
 }
 
@@ -159,35 +161,20 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
                int nb, int nout, cudaStream_t st) {
   const int v = mul_variant_for(na, nb, nout);
   switch (v) {
-    case 12: return launch_mul_tc(a, b, out, count, na, nb, nout, st);
+    case 12: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 0);
+    case 13: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 64);
+    case 14: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 128);
+    case 15: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 256);
     case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
-    case 11: return launch_kara<28, 8, 128>(a, b, out, count, na, st);
-    case 2: return launch_variant<29, 8, 32>(a, b, out, count, na, nb, nout, st);
-    case 3: return launch_variant<29, 4, 32>(a, b, out, count, na, nb, nout, st);
-    case 4: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);
-    case 5: return launch_variant<30, 8, 8>(a, b, out, count, na, nb, nout, st);
-    case 6: return launch_variant<29, 8, 32, true>(a, b, out, count, na, nb, nout, st);
-    case 7: return launch_variant<28, 16, 128, false, true>(a, b, out, count, na, nb, nout, st);
-    case 8: return launch_variant<29, 16, 32, false, true>(a, b, out, count, na, nb, nout, st);
-    case 9: return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout, st);
-    default: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
+    case 9: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
+    default: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);
   }
 }
 
 int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                      int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                     cudaStream_t st);
+                     cudaStream_t st, int force_nt);
 
-// The low nout limbs of a batch of products whose instances lie at strides
-// sa, sb, so (limbs) -- operands and results inside larger per-instance
-// records, as the step-batched division keeps them.  The tensor-core
-// product runs where launch_mul would pick it (band start lo: limbs >= lo + 2
-// are floor(a b / B^j) or one unit more, see tc_product); other shapes run
-// the integer product exactly (lo ignored: exact is within the band's
-// bound).  abort_flag: set if a tensor-core CTA gave up at a wait limit.
-// tc_min: shorter operand (limbs) from which the tensor cores are used.
-// sk_ws, sk_bytes: room for the column sums of the split-K form, which few
-// large products take (null: never).
 size_t mul_sk_bytes_per_product(int na, int nb, int nout, int lo);
 bool mul_sk_worth(int64_t count, int na, int nb, int nout, int lo);
 int launch_mul_tc_sk(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
@@ -206,13 +193,12 @@ int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, 
           sk_bytes >= (size_t)count * mul_sk_bytes_per_product(na, nb, nout, lo))
         return launch_mul_tc_sk(a, sa, b, sb, out, so, count, na, nb, nout, lo, sk_ws, sk_bytes,
                                 abort_flag, st);
-      return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st);
+      return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st, 0);
     }
   }
   const int nmax = na > nb ? na : nb;
-  if (nmax < 1536) return launch_variant<28, 8, 128, false, true>(a, b, out, count, na, nb, nout,
-                                                                 st, sa, sb, so);
-  return launch_variant<29, 16, 32, false, true>(a, b, out, count, na, nb, nout, st, sa, sb, so);
+  if (nmax < 1536) return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st, sa, sb, so);
+  return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st, sa, sb, so);
 }
 
 }  // namespace bigint

@@ -109,29 +109,6 @@ __device__ __forceinline__ void finish_chunk(uint64_t (&acc)[Q], uint64_t X, int
     atomicOr(reinterpret_cast<unsigned long long *>(out + limb), cur);
 }
 
-// ASM selects how the digit product is written: as one explicit
-// mad.wide.u32 per product, or as a C++ 64-bit multiply-add that the
-// compiler maps to IMAD.WIDE.U32 (and may schedule differently).
-template <int Q, int T0, bool ASM>
-__device__ __forceinline__ void row_steps(uint64_t (&acc)[Q], const uint32_t (&W)[2 * Q],
-                                          const uint32_t *a) {
-  if constexpr (T0 < Q) {
-    const uint4 av = *reinterpret_cast<const uint4 *>(a + T0);
-    const uint32_t a4[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-#pragma unroll
-      for (int q = 0; q < Q; q++) {  // one IMAD.WIDE.U32 per digit product
-        if constexpr (ASM)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a4[t]), "r"(W[Q - (T0 + t) + q]));
-        else
-          acc[q] += (uint64_t)a4[t] * (uint64_t)W[Q - (T0 + t) + q];
-      }
-    }
-    row_steps<Q, T0 + 4, ASM>(acc, W, a);
-  }
-}
-
 // Row steps with the window split in two register buffers (lo = digits
 // [base-Q, base), hi = [base, base+Q)); the caller swaps the roles of the two
 // buffers from one group to the next, so the window slides with no register
@@ -231,60 +208,13 @@ __device__ __forceinline__ void conv_unit_pp(int u, int KR, int KW, const uint32
   }
 }
 
-template <int RB, int Q, int F, bool ASM>
-__device__ __forceinline__ void conv_unit(int u, int KR, int KW, const uint32_t *sRow,
-                                          const uint32_t *sW, uint64_t *out, int nout,
-                                          uint64_t *sH) {
-  static_assert(F % Q == 0, "flush interval must be a whole number of groups");
-  // F digit products of 2RB bits, plus a normalised digit and an incoming
-  // carry, must fit the 64-bit accumulator
-  static_assert(F < (1 << (64 - 2 * RB)), "flush interval too long for this digit size");
-  constexpr int FG = F / Q;
-  const int NWp = KW * Q;
-  const bool pair = u < KR;
-  const int switch_g = pair ? u + 1 : -1;
-  uint64_t acc[Q], X = 0;
-  uint32_t W[2 * Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) acc[q] = 0;
-#pragma unroll
-  for (int q = 0; q < Q; q += 4) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(sW + u * Q + q);
-    W[Q + q] = v.x; W[Q + q + 1] = v.y; W[Q + q + 2] = v.z; W[Q + q + 3] = v.w;
-  }
-  bool fwd = true;
-#pragma unroll 1
-  for (int g = 0; g <= KR; g++) {
-    if (g == switch_g) {  // low chunk done: continue with its partner
-      finish_chunk<RB, Q>(acc, X, u, out, nout, sH);
-#pragma unroll
-      for (int q = 0; q < Q; q++) { acc[q] = 0; W[Q + q] = 0; }  // window[NWp..) is padding
-      X = 0;
-      fwd = false;
-    }
-    const int base = fwd ? (u - g) * Q : NWp + (u + 1 - g) * Q;
-    const int i0 = fwd ? g * Q : (g - 1) * Q;
-#pragma unroll
-    for (int q = 0; q < Q; q += 4) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(sW + base - Q + q);
-      W[q] = v.x; W[q + 1] = v.y; W[q + 2] = v.z; W[q + 3] = v.w;
-    }
-    row_steps<Q, 0, ASM>(acc, W, sRow + i0);
-#pragma unroll
-    for (int q = 0; q < Q; q++) W[Q + q] = W[q];
-    if ((g + 1) % FG == 0) normalise<RB, Q>(acc, X);
-  }
-  finish_chunk<RB, Q>(acc, X, pair ? KW + u : u, out, nout, sH);
-}
-
 // Low nout limbs of x[0..nx) * y[0..ny) into out[0..nout) (out must not
-// overlap x or y).  With BAND (which needs PP), chunks at or above limb nout
-// are skipped, and lo > 0 allows the result to miss the products of chunks
+// overlap x or y).  With BAND, chunks at or above limb nout are skipped, and lo > 0 allows the result to miss the products of chunks
 // below limb lo (see conv_unit_pp): limbs >= lo + 2 are then at most a few
 // units of limb lo below the exact value.  smem: blk_mul_smem_words<RB,Q>(nx, ny) words, 16-byte
 // aligned.  Returns the carry out of limb nout-1 of the final addition
 // (0 whenever nout >= nx + ny).
-template <int RB, int Q, int F, bool ASM = false, bool PP = false, bool BAND = false>
+template <int RB, int Q, int F, bool BAND = false>
 __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny, uint64_t *out,
                             int nout, uint32_t *smem, int lo = 0) {
   const int NX = Digits<RB>::count(nx), NY = Digits<RB>::count(ny);
@@ -309,8 +239,7 @@ __device__ uint32_t blk_mul(const uint64_t *x, int nx, const uint64_t *y, int ny
 
   // ---- A3: convolution, one unit at a time per thread
   for (int u = t; u < KW; u += T) {
-    if constexpr (PP) conv_unit_pp<RB, Q, F, BAND>(u, KR, KW, sRow, sW, out, nout, sH, lo);
-    else conv_unit<RB, Q, F, ASM>(u, KR, KW, sRow, sW, out, nout, sH);
+    conv_unit_pp<RB, Q, F, BAND>(u, KR, KW, sRow, sW, out, nout, sH, lo);
   }
   __syncthreads();
 
@@ -343,7 +272,7 @@ template <int RB, int Q, int F>
 __device__ __noinline__ uint32_t blk_mul_call(const uint64_t *x, int nx, const uint64_t *y,
                                               int ny, uint64_t *out, int nout, uint32_t *smem,
                                               int lo) {
-  return blk_mul<RB, Q, F, false, true, true>(x, nx, y, ny, out, nout, smem, lo);
+  return blk_mul<RB, Q, F, true>(x, nx, y, ny, out, nout, smem, lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,7 +299,7 @@ __host__ __device__ constexpr int blk_kara_units(int n) {
   return blk_mul_units<RB, Q>(hh + 1, hh + 1);
 }
 
-template <int RB, int Q, int F, bool PP>
+template <int RB, int Q, int F>
 __device__ void blk_mul_kara(const uint64_t *x, const uint64_t *y, int n, uint64_t *out,
                              uint32_t *smem) {
   const int h = n / 2, hh = n - h;  // x0, y0: h limbs; x1, y1: hh limbs
@@ -399,10 +328,10 @@ __device__ void blk_mul_kara(const uint64_t *x, const uint64_t *y, int n, uint64
     __syncthreads();
   }
   // z1 = s1 s2 (into shared memory)
-  blk_mul<RB, Q, F, false, PP>(s1, hh + 1, s2, hh + 1, z1, nz1, msm);
+  blk_mul<RB, Q, F>(s1, hh + 1, s2, hh + 1, z1, nz1, msm);
   // z0 = x0 y0 -> out[0, 2h); z2 = x1 y1 -> out[2h, 2n)
-  blk_mul<RB, Q, F, false, PP>(x, h, y, h, out, 2 * h, msm);
-  blk_mul<RB, Q, F, false, PP>(x + h, hh, y + h, hh, out + 2 * h, 2 * hh, msm);
+  blk_mul<RB, Q, F>(x, h, y, h, out, 2 * h, msm);
+  blk_mul<RB, Q, F>(x + h, hh, y + h, hh, out + 2 * h, 2 * hh, msm);
   {  // z1 -= z0; z1 -= z2 (the difference x0 y1 + x1 y0 is nonnegative)
     auto l0 = [&](int j) { return make_ulonglong2(z1[j], j < 2 * h ? out[j] : 0ull); };
     auto st = [&](int j, uint64_t v) { z1[j] = v; };

@@ -50,10 +50,9 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
       for (int k = 0; k < 8; k++)
         asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(m), "r"(m));
     }
-  } else if constexpr (VARIANT == 3 || VARIANT == 4) {
+  } else {
     // the multiply kernel's inner step: 8 column accumulators, a sliding
-    // window of 16 digits; 3 = one mad.wide.u32 per product (the kernel's
-    // form), 4 = the same step written as a C++ 64-bit multiply-add
+    // window of 16 digits, one mad.wide.u32 per digit product
     uint64_t acc[8];
     uint32_t W[16];
 #pragma unroll
@@ -66,57 +65,14 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
       for (int t = 0; t < 8; t++) {
         const uint32_t a = x[t] ^ (uint32_t)it;
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-          if constexpr (VARIANT == 3)
-            asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a), "r"(W[8 - t + q]));
-          else
-            acc[q] += (uint64_t)a * W[8 - t + q];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; q++) W[8 + q] = W[q] + (uint32_t)it;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; q++) y[q] += acc[q];
-  } else if constexpr (VARIANT == 5) {
-    // as 0 (8 independent chains) in the C++ 64-bit multiply-add form
-#pragma unroll 1
-    for (int it = 0; it < PROBE_ITERS; it++) {
-#pragma unroll
-      for (int k = 0; k < 8; k++) y[k] += (uint64_t)x[k] * m;
-      x[it & 7] += (uint32_t)y[(it + 3) & 7];
-    }
-  } else if constexpr (VARIANT == 6) {
-    // sliding window, asm form, but the row digit differs per product (no
-    // operand reused between consecutive instructions)
-    uint64_t acc[8];
-    uint32_t W[16];
-#pragma unroll
-    for (int q = 0; q < 8; q++) acc[q] = x[q];
-#pragma unroll
-    for (int q = 0; q < 16; q++) W[q] = x[(q + 3) & 7] + q;
-#pragma unroll 1
-    for (int it = 0; it < PROBE_ITERS / 8; it++) {
-#pragma unroll
-      for (int t = 0; t < 8; t++) {
-#pragma unroll
         for (int q = 0; q < 8; q++)
-          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(x[(t + q) & 7]), "r"(W[8 - t + q]));
+          asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[q]) : "r"(a), "r"(W[8 - t + q]));
       }
 #pragma unroll
       for (int q = 0; q < 8; q++) W[8 + q] = W[q] + (uint32_t)it;
     }
 #pragma unroll
     for (int q = 0; q < 8; q++) y[q] += acc[q];
-  } else {
-    // 8 independent chains, asm form, both multiplicands per-thread and
-    // different in every instruction
-#pragma unroll 1
-    for (int it = 0; it < PROBE_ITERS; it++) {
-#pragma unroll
-      for (int k = 0; k < 8; k++)
-        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(y[k]) : "r"(x[k]), "r"(x[(k + 3) & 7]));
-    }
   }
   __syncthreads();
   if (threadIdx.x == 0) cycles[blockIdx.x] = clock64() - t0;
@@ -128,9 +84,7 @@ __global__ void __launch_bounds__(256) k_probe(uint32_t seed, uint64_t *sink, lo
 
 // Operations per thread for one probe launch.
 static double probe_ops_per_thread(int variant) {
-  if (variant == 3 || variant == 4) return (double)(PROBE_ITERS / 8) * 64;
-  if (variant == 5 || variant == 7) return (double)PROBE_ITERS * 8;
-  if (variant == 6) return (double)(PROBE_ITERS / 8) * 64;
+  if (variant == 3) return (double)(PROBE_ITERS / 8) * 64;
   return (double)PROBE_ITERS * 8;
 }
 
@@ -178,10 +132,6 @@ int probe_int_throughput(int variant, double *ops, double *mhz) {
     case 1: return run_probe<1>(ops, mhz);
     case 2: return run_probe<2>(ops, mhz);
     case 3: return run_probe<3>(ops, mhz);
-    case 4: return run_probe<4>(ops, mhz);
-    case 5: return run_probe<5>(ops, mhz);
-    case 6: return run_probe<6>(ops, mhz);
-    case 7: return run_probe<7>(ops, mhz);
     default: return BIGINT_EINVAL;
   }
 }

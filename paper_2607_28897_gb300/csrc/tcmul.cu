@@ -306,9 +306,12 @@ static long tc_blocks(int nx, int ny, int nout, int lo, int NT, bool XC) {
 static int tc_nt(TcShape sh) { return sh == TC_256 ? 256 : (sh >= TC_128_XC ? 128 : 64); }
 static bool tc_xc(TcShape sh) { return sh == TC_64_XC || sh == TC_128_XC || sh == TC_256; }
 
+// force_nt: 0 (the tile by the columns computed, as below) or the tile's
+// column count 64, 128 or 256 (the autotuner's candidates); a forced 64- or
+// 128-column tile drops x's carry digit where that saves a tile.
 int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                      int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                     cudaStream_t st) {
+                     cudaStream_t st, int force_nt) {
   TcArgs A{a, b, out, sa, sb, so, lo, abort_flag};
   int nx = na, ny = nb;
   if (nb < na) {
@@ -324,7 +327,13 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
   // the blocks issued (a low product whose longer operand has most of the
   // columns); the longer operand then has to fit shared memory as x.
   TcShape sh = tc_shape_cols(nx, ny, nout, lo);
-  if (nx != ny && ny <= 16383) {
+  if (force_nt == 256) {
+    sh = TC_256;
+  } else if (force_nt == 64 || force_nt == 128) {
+    const bool drop = tc_blocks(nx, ny, nout, lo, force_nt, false) <
+                      tc_blocks(nx, ny, nout, lo, force_nt, true);
+    sh = force_nt == 64 ? (drop ? TC_64_NOXC : TC_64_XC) : (drop ? TC_128_NOXC : TC_128_XC);
+  } else if (nx != ny && ny <= 16383) {
     const TcShape sw = tc_shape_cols(ny, nx, nout, lo);
     const long keep = tc_blocks(nx, ny, nout, lo, tc_nt(sh), tc_xc(sh));
     const long swap = tc_blocks(ny, nx, nout, lo, tc_nt(sw), tc_xc(sw));
@@ -356,8 +365,8 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
 }
 
 int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
-                  int nb, int nout, cudaStream_t st) {
-  return launch_mul_tc_ex(a, na, b, nb, out, nout, count, na, nb, nout, 0, nullptr, st);
+                  int nb, int nout, cudaStream_t st, int force_nt) {
+  return launch_mul_tc_ex(a, na, b, nb, out, nout, count, na, nb, nout, 0, nullptr, st, force_nt);
 }
 
 // ---- split-K products (host) --------------------------------------------------

@@ -1,9 +1,10 @@
 // tune.cu -- the autotuner and its persistent table.
 //
 // Two knobs are tuned by timing on the caller's own data:
-//   * the multiply variant (digit size RB, chunk width Q -- the "limbs per
-//     thread" of the paper's sequentialisation factor -- and the carry
-//     interval) per operand size class;
+//   * the multiply variant per operand size class: the tensor-core product's
+//     tile (64, 128 or 256 output columns per tile, i.e. three, two or one
+//     CTAs per SM) or an integer product (digit size RB and chunk width Q --
+//     the "limbs per thread" of the paper's sequentialisation factor);
 //   * the CTA size ("threads per instance") of persistent batch launches.
 // The table is saved as a small JSON file keyed by the GPU name.
 #include <cstdio>
@@ -18,6 +19,8 @@ namespace bigint {
 int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                int nb, int nout, cudaStream_t st);
 int mul_set_variant(int v);
+bool mul_variant_valid(int v);
+size_t mul_tc_smem(int na, int nb);
 int mul_size_class(int na, int nb);
 extern int g_mul_tuned[32];
 int batch_set_threads(int t);
@@ -26,7 +29,9 @@ int batch_configure(bigint_batch *B);
 int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status,
                  void *ws, int mode, cudaStream_t st);
 size_t batch_workspace_bytes(const bigint_batch *B);
-int batch_retune(bigint_batch *B, int threads);
+int batch_retune(bigint_batch *B, int threads, int use_tc);
+bool batch_uses_tc(const bigint_batch *B);
+int batch_threads_of(const bigint_batch *B);
 
 namespace {
 
@@ -62,19 +67,33 @@ std::string gpu_name() {
 
 }  // namespace
 
+// Candidates of the multiply tuner for an na x nb product: the tensor-core
+// product with its tile chosen by size (12) and forced to 64, 128 and 256
+// output columns (13, 14, 15) -- the tile also sets how many CTAs share an
+// SM -- and the integer products with 29-bit digits / 16-column chunks (8)
+// and 28-bit digits / 8-column chunks (9), plus one level of Karatsuba (10)
+// for square products.
 int tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na, int nb,
              cudaStream_t st, int *best_variant) {
+  int cand[8], nc = 0;
+  if ((na < nb ? na : nb) >= 64 && mul_tc_smem(na, nb) > 0) {
+    cand[nc++] = 12; cand[nc++] = 13; cand[nc++] = 14; cand[nc++] = 15;
+  }
+  cand[nc++] = 8;
+  cand[nc++] = 9;
+  if (na == nb && na >= 64) cand[nc++] = 10;
   int best = 0;
   float best_ms = 1e30f;
-  for (int v = 1; v <= 6; v++) {
-    mul_set_variant(v);
+  for (int i = 0; i < nc; i++) {
+    if (mul_set_variant(cand[i]) != BIGINT_OK) continue;
     float ms = 0;
     const int rc = time_best([&] { return launch_mul(a, b, out, count, na, nb, na + nb, st); },
                              st, 2, &ms);
     if (rc == BIGINT_OK && ms < best_ms) {
       best_ms = ms;
-      best = v;
+      best = cand[i];
     }
+    if (rc != BIGINT_OK) cudaGetLastError();  // a candidate that does not fit this shape
   }
   mul_set_variant(0);
   if (best == 0) return BIGINT_EINTERNAL;
@@ -83,15 +102,23 @@ int tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
   return BIGINT_OK;
 }
 
+// Candidates of the batch tuner: the launch whose CTAs hold their SM's
+// tensor memory and run the large products on the tensor cores (when the
+// batch has such products), and launches on the integer pipes alone with
+// 256, 384 or 512 threads per CTA (threads per instance).  *best_threads
+// receives the chosen CTA size (tcm::TC_CTA_THREADS for the tensor-core
+// form).
 int tune_batch(bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *status, void *ws,
                size_t bytes, cudaStream_t st, int *best_threads) {
   if (bytes < batch_workspace_bytes(B)) return BIGINT_ENOMEM;
-  static const int cand[] = {256, 384, 512};
-  int best = 0;
+  struct Cand { bool tc; int threads; };
+  const Cand cand[] = {{true, 0}, {false, 256}, {false, 384}, {false, 512}};
+  int best = -1;
   float best_ms = 1e30f;
-  for (int T : cand) {
-    int rc = batch_retune(B, T);
+  for (int i = 0; i < 4; i++) {
+    int rc = batch_retune(B, cand[i].threads, cand[i].tc ? 1 : 0);
     if (rc != BIGINT_OK) return rc;
+    if (cand[i].tc && !batch_uses_tc(B)) continue;  // nothing for the tensor cores
     if (batch_workspace_bytes(B) > bytes) continue;  // needs more resident CTAs than budgeted
     float ms = 0;
     rc = time_best([&] { return batch_launch(B, in, out, status, ws, BIGINT_BATCH_PERSISTENT, st); },
@@ -99,13 +126,13 @@ int tune_batch(bigint_batch *B, const uint64_t *in, uint64_t *out, int32_t *stat
     if (rc != BIGINT_OK) return rc;
     if (ms < best_ms) {
       best_ms = ms;
-      best = T;
+      best = i;
     }
   }
-  if (best == 0) return BIGINT_EINTERNAL;
-  batch_set_threads(best);
-  const int rc = batch_retune(B, best);
-  if (best_threads) *best_threads = best;
+  if (best < 0) return BIGINT_EINTERNAL;
+  if (!cand[best].tc) batch_set_threads(cand[best].threads);
+  const int rc = batch_retune(B, cand[best].threads, cand[best].tc ? 1 : 0);
+  if (best_threads) *best_threads = batch_threads_of(B);
   return rc;
 }
 
@@ -150,7 +177,7 @@ int tuning_load(const char *path) {
     int v = 0, used = 0;
     if (m == std::string::npos || std::sscanf(text.c_str() + m + 1, " %d%n", &v, &used) != 1)
       return BIGINT_EINVAL;
-    if (v < 0 || v > 6) return BIGINT_EINVAL;
+    if (!mul_variant_valid(v)) return BIGINT_EINVAL;
     classes[c] = v;
     m = text.find(c < 31 ? ',' : ']', m + 1);
   }

@@ -121,10 +121,14 @@ def test_tuning_table_rejects_other_gpu(L, tmp_path):
     f = tmp_path / "t.json"
     f.write_text('{"gpu": "some other GPU", "batch_threads": 256, '
                  '"mul_variant_by_class": [' + ", ".join(["0"] * 32) + "]}")
-    assert L.bigint_tuning_load(str(f).encode()) == bi.EINVAL
-    assert L.bigint_tuning_load(b"/nonexistent/tuning.json") == bi.EINVAL
+    assert L.bigint_load_tuning(str(f).encode()) == bi.EINVAL
+    assert L.bigint_load_tuning(b"/nonexistent/tuning.json") == bi.EINVAL
     assert L.bigint_set_variant(0, 99) == bi.EINVAL
     assert L.bigint_set_variant(7, 0) == bi.EINVAL
+    for v in (1, 3, 7, 11):  # integer forms the library no longer carries
+        assert L.bigint_set_variant(0, v) == bi.EINVAL
+    for v in (8, 9, 10, 12, 13, 14, 15, 0):
+        assert L.bigint_set_variant(0, v) == bi.OK
 
 
 # ---- host-buffer entry points: argument checks that need no GPU -------------

@@ -112,7 +112,7 @@ def test_batch_tune_and_graph(orc):
     st = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
     B = bi.Batch(ops)
     best = B.tune(dpool, dout, st)
-    assert best in (256, 384, 512)
+    assert best in (256, 384, 512, 544)  # 544: the tensor-core form
     dout.zero_()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())

@@ -87,12 +87,12 @@ def test_config_sweep_full_size(bi, orc, n):
     assert np.array_equal(p[idx], orc.batch_mul(a[idx], b[idx]))
 
 
-@pytest.mark.parametrize("variant", range(1, 12))
+@pytest.mark.parametrize("variant", [8, 9, 10, 12, 13, 14, 15])
 @pytest.mark.parametrize("n", [1, 63, 64, 65, 511, 1000, 2049])
 def test_every_variant(bi, orc, variant, n):
-    """Every multiply variant (digit size, chunk width, window form,
-    Karatsuba) gives the oracle's product; Karatsuba variants fall back to
-    the schoolbook kernel below 64 limbs."""
+    """Every multiply variant (integer digit size and chunk width, Karatsuba,
+    the tensor-core product with each tile) gives the oracle's product;
+    Karatsuba falls back to the schoolbook kernel below 64 limbs."""
     from paper_2607_28897_gb300 import inputs
 
     a = inputs.limbs(700 + n, 3, n)
