@@ -205,7 +205,9 @@ int bigint_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w,
  * from the start of the pool.  Each operation is exactly the uniform entry
  * point's computation (same kernels' block routines), so results do not
  * depend on the batch an operation runs in.
- *   ADD/SUB: out[o1 .. o1+na) = a +- b (na == nb); status = carry / borrow
+ *   ADD/SUB: out[o1 .. o1+n) = a +- b, n = na = nb, or n = max(na, nb)
+ *            with the flag BIGINT_ZEXT in `flags` (the shorter operand
+ *            zero-extended); status = carry / borrow
  *   MUL:     out[o1 .. o1+na+nb) = a * b (na, nb <= BIGINT_MUL_MAX_LIMBS)
  *   DIVMOD:  u = a (na limbs), v = b (nb limbs); q at o1 (max(na-nb+1,1)
  *            limbs), r at o2 (nb limbs); status as for bigint_divmod.
@@ -214,10 +216,13 @@ int bigint_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w,
 #define BIGINT_OP_SUB 2
 #define BIGINT_OP_MUL 3
 #define BIGINT_OP_DIVMOD 4
+/* ADD/SUB with operands of different lengths: zero-extend the shorter one
+ * (without it such an operation is rejected with BIGINT_EINVAL). */
+#define BIGINT_ZEXT 1
 typedef struct {
   int32_t op;        /* BIGINT_OP_*                                       */
   int32_t na, nb;    /* limbs of a and b                                  */
-  int32_t reserved;  /* 0                                                 */
+  int32_t flags;     /* 0 or BIGINT_ZEXT (ADD/SUB only)                   */
   int64_t a, b;      /* input offsets (limbs)                             */
   int64_t o1, o2;    /* output offsets (limbs)                            */
 } bigint_op;
@@ -247,6 +252,71 @@ int bigint_batch_upload(bigint_batch *batch, void *workspace, size_t bytes,
 int bigint_batch_launch(const bigint_batch *batch, const uint64_t *in_pool,
                         uint64_t *out_pool, int32_t *status, void *workspace,
                         int mode, void *stream);
+/* ---- ragged views and the per-operation ragged forms ---------------------
+ * A view is a batch of `count` integers of possibly different lengths whose
+ * limbs lie in DEVICE memory at `data` (8-byte aligned): instance i has
+ * nlimbs[i] limbs starting offset[i] limbs from data -- or, with offset /
+ * nlimbs NULL, the uniform layout of n limbs at i*n.  offset and nlimbs are
+ * HOST arrays (the shapes are needed on the host to plan the launch), read
+ * during the call only.  bigint_batch_cview is the read-only view of the
+ * inputs, bigint_batch_view the view of the outputs.                       */
+typedef struct {
+  const uint64_t *data;   /* device limbs                                   */
+  const int64_t *offset;  /* host, count entries, or NULL (instance i at i*n) */
+  const int32_t *nlimbs;  /* host, count entries, or NULL (every length n)  */
+  int64_t count;
+  int32_t n;              /* uniform length where nlimbs is NULL            */
+} bigint_batch_cview;
+typedef struct {
+  uint64_t *data;
+  const int64_t *offset;
+  const int32_t *nlimbs;
+  int64_t count;
+  int32_t n;
+} bigint_batch_view;
+
+/* The operations of Sec. V over ragged batches, instance by instance, as
+ * one persistent launch of the batched form (the kernels above: each
+ * instance's result is that of the uniform entry point).  All views have
+ * the same count; the output lengths must be the results' lengths:
+ *   add / sub: max(na, nb) limbs (na == nb unless flags has BIGINT_ZEXT,
+ *     which zero-extends the shorter operand); carry_out / borrow_out:
+ *     count int32 (0 or 1), or NULL
+ *   mul: na + nb limbs (na, nb <= BIGINT_MUL_MAX_LIMBS)
+ *   divmod: q of max(nu - nv + 1, 1) limbs, r of nv limbs; status as for
+ *     bigint_divmod, count int32, or NULL
+ * Output instances must not overlap each other or the inputs.  workspace:
+ * bigint_batch_views_workspace(op, a, b) bytes of device memory, 256-byte
+ * aligned.  The call plans on the host and copies the plan to the device
+ * from pageable memory, which waits for the stream's earlier work; the
+ * launch itself is asynchronous.  BIGINT_EINVAL for malformed views or
+ * mismatched lengths, BIGINT_ENOMEM for a short workspace.                */
+size_t bigint_batch_views_workspace(int op, const bigint_batch_cview *a,
+                                    const bigint_batch_cview *b);
+int bigint_batch_add(const bigint_batch_cview *a, const bigint_batch_cview *b,
+                     const bigint_batch_view *out, int32_t *carry_out, int flags,
+                     void *workspace, size_t bytes, void *stream);
+int bigint_batch_sub(const bigint_batch_cview *a, const bigint_batch_cview *b,
+                     const bigint_batch_view *out, int32_t *borrow_out, int flags,
+                     void *workspace, size_t bytes, void *stream);
+int bigint_batch_mul(const bigint_batch_cview *a, const bigint_batch_cview *b,
+                     const bigint_batch_view *out, void *workspace, size_t bytes,
+                     void *stream);
+int bigint_batch_divmod(const bigint_batch_cview *u, const bigint_batch_cview *v,
+                        const bigint_batch_view *q, const bigint_batch_view *r,
+                        int32_t *status, void *workspace, size_t bytes, void *stream);
+
+/* A mixed batch of bigint_op descriptors in one call: plan, upload and
+ * launch (mode: BIGINT_BATCH_PERSISTENT or BIGINT_BATCH_PER_CLASS) -- the
+ * create / upload / launch / destroy sequence above without keeping the
+ * plan (for a batch run once; keep the plan with bigint_batch_create to
+ * launch it repeatedly or capture it in a CUDA graph).  workspace:
+ * bigint_batch_run_workspace(ops, nops) bytes, 256-byte aligned.           */
+size_t bigint_batch_run_workspace(const bigint_op *ops, int64_t nops);
+int bigint_batch_run(const bigint_op *ops, int64_t nops, const uint64_t *in_pool,
+                     uint64_t *out_pool, int32_t *status, void *workspace, size_t bytes,
+                     int mode, void *stream);
+
 /* Autotuner of the batched form: times the persistent launch on this batch
  * (synchronous) in each candidate form -- large products on the tensor
  * cores (CTAs of 544 threads holding their SM's tensor memory; only if the

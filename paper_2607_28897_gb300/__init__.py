@@ -60,6 +60,13 @@ SIGNATURES = {
     "bigint_batch_tune": ([_P, _P, _P, _P, _P, _SZ, _P, ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "bigint_batch_destroy": ([_P], None),
+    "bigint_batch_views_workspace": ([ctypes.c_int, _P, _P], _SZ),
+    "bigint_batch_add": ([_P, _P, _P, _P, ctypes.c_int, _P, _SZ, _P], ctypes.c_int),
+    "bigint_batch_sub": ([_P, _P, _P, _P, ctypes.c_int, _P, _SZ, _P], ctypes.c_int),
+    "bigint_batch_mul": ([_P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+    "bigint_batch_divmod": ([_P, _P, _P, _P, _P, _P, _SZ, _P], ctypes.c_int),
+    "bigint_batch_run_workspace": ([_P, _I64], _SZ),
+    "bigint_batch_run": ([_P, _I64, _P, _P, _P, _P, _SZ, ctypes.c_int, _P], ctypes.c_int),
     "bigint_tune": ([_P, _P, _P, _I64, _I32, _I32, _P, ctypes.POINTER(ctypes.c_int)],
                         ctypes.c_int),
     "bigint_save_tuning": ([ctypes.c_char_p], ctypes.c_int),
@@ -507,7 +514,7 @@ def op_dtype():
     """numpy dtype of one bigint_op descriptor (include/bigint.h)."""
     import numpy as np
 
-    return np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("reserved", "<i4"),
+    return np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("flags", "<i4"),
                      ("a", "<i8"), ("b", "<i8"), ("o1", "<i8"), ("o2", "<i8")])
 
 
@@ -589,3 +596,94 @@ def save_tuning(path: str) -> None:
 
 def load_tuning(path: str) -> None:
     _check(load().bigint_load_tuning(path.encode()), "bigint_load_tuning")
+
+
+# ---- ragged views -----------------------------------------------------------
+class _View(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+                ("nlimbs", ctypes.c_void_p), ("count", ctypes.c_int64), ("n", ctypes.c_int32)]
+
+
+ZEXT = 1
+
+
+def view(data, offsets=None, nlimbs=None, count=None, n=0):
+    """A ragged view (bigint_batch_cview / bigint_batch_view) over a 1-D or
+    2-D CUDA limb tensor: instance i has nlimbs[i] limbs starting offsets[i]
+    limbs into `data` (numpy int64 / int32 host arrays), or the uniform
+    layout of a (count, n) tensor.  Returns the ctypes structure; it keeps
+    the host arrays alive."""
+    import numpy as np
+
+    if not data.is_cuda:
+        raise TypeError("view data must be a CUDA tensor")
+    v = _View()
+    v.data = data.data_ptr()
+    if offsets is None:
+        count, n = data.shape if data.dim() == 2 else (count, n)
+        v.offset = v.nlimbs = None
+    else:
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        nlimbs = np.ascontiguousarray(nlimbs, dtype=np.int32)
+        count = offsets.size
+        v.offset, v.nlimbs = offsets.ctypes.data, nlimbs.ctypes.data
+        v._keep = (offsets, nlimbs)
+    v.count, v.n = int(count), int(n)
+    return v
+
+
+def views_workspace_bytes(op: int, a, b) -> int:
+    return int(load().bigint_batch_views_workspace(op, ctypes.byref(a), ctypes.byref(b)))
+
+
+def _views_ws(op, a, b, workspace, device):
+    torch = _torch()
+    if workspace is None:
+        workspace = torch.empty(max(views_workspace_bytes(op, a, b), 256), dtype=torch.uint8,
+                                device=device)
+    return workspace
+
+
+def batch_add(a, b, out, carry=None, zext=False, workspace=None, stream=None, sub=False):
+    """out = a + b (or a - b with sub=True) over ragged views; carry: a CUDA
+    int32 tensor of count entries or None."""
+    op = OP_SUB if sub else OP_ADD
+    ws = _views_ws(op, a, b, workspace, "cuda")
+    fn = load().bigint_batch_sub if sub else load().bigint_batch_add
+    rc = fn(ctypes.byref(a), ctypes.byref(b), ctypes.byref(out),
+            carry.data_ptr() if carry is not None else None, ZEXT if zext else 0,
+            ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(rc, "bigint_batch_sub" if sub else "bigint_batch_add")
+
+
+def batch_mul(a, b, out, workspace=None, stream=None):
+    ws = _views_ws(OP_MUL, a, b, workspace, "cuda")
+    _check(load().bigint_batch_mul(ctypes.byref(a), ctypes.byref(b), ctypes.byref(out),
+                                   ws.data_ptr(), ws.numel(), _stream_ptr(stream)),
+           "bigint_batch_mul")
+
+
+def batch_divmod(u, v, q, r, status=None, workspace=None, stream=None):
+    ws = _views_ws(OP_DIVMOD, u, v, workspace, "cuda")
+    _check(load().bigint_batch_divmod(ctypes.byref(u), ctypes.byref(v), ctypes.byref(q),
+                                      ctypes.byref(r),
+                                      status.data_ptr() if status is not None else None,
+                                      ws.data_ptr(), ws.numel(), _stream_ptr(stream)),
+           "bigint_batch_divmod")
+
+
+def batch_run(ops, in_pool, out_pool, status=None, mode=BATCH_PERSISTENT, workspace=None,
+              stream=None):
+    """Plans, uploads and launches a mixed batch of descriptors in one call."""
+    import numpy as np
+
+    torch = _torch()
+    ops = np.ascontiguousarray(ops, dtype=op_dtype())
+    L = load()
+    need = int(L.bigint_batch_run_workspace(ops.ctypes.data, len(ops)))
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=in_pool.device)
+    _check(L.bigint_batch_run(ops.ctypes.data, len(ops), in_pool.data_ptr(), out_pool.data_ptr(),
+                              status.data_ptr() if status is not None else None,
+                              workspace.data_ptr(), workspace.numel(), mode, _stream_ptr(stream)),
+           "bigint_batch_run")

@@ -43,12 +43,17 @@ __device__ __forceinline__ int op_status(const OpDev &o, const uint64_t *in, uin
   switch (o.op) {
     case BIGINT_OP_ADD:
     case BIGINT_OP_SUB: {
+      // operands of different lengths (BIGINT_ZEXT) are zero-extended to
+      // the longer one, which is the result's length
       const uint64_t *a = in + o.a, *b = in + o.b;
       uint64_t *r = out + o.o1;
-      auto load = [&](int j) { return make_ulonglong2(a[j], b[j]); };
+      const int n = o.na > o.nb ? o.na : o.nb;
+      auto load = [&](int j) {
+        return make_ulonglong2(j < o.na ? a[j] : 0ull, j < o.nb ? b[j] : 0ull);
+      };
       auto store = [&](int j, uint64_t x) { r[j] = x; };
-      return o.op == BIGINT_OP_ADD ? (int)blk_addsub<false>(o.na, 0u, load, store, scr)
-                                   : (int)blk_addsub<true>(o.na, 0u, load, store, scr);
+      return o.op == BIGINT_OP_ADD ? (int)blk_addsub<false>(n, 0u, load, store, scr)
+                                   : (int)blk_addsub<true>(n, 0u, load, store, scr);
     }
     case BIGINT_OP_MUL:
       if constexpr (TC) {
@@ -119,7 +124,7 @@ namespace {
 double op_cost(const bigint_op &o) {
   switch (o.op) {
     case BIGINT_OP_ADD:
-    case BIGINT_OP_SUB: return (double)o.na;
+    case BIGINT_OP_SUB: return (double)(o.na > o.nb ? o.na : o.nb);
     case BIGINT_OP_MUL: return (double)o.na * o.nb;
     case BIGINT_OP_DIVMOD: {
       const double nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
@@ -170,7 +175,7 @@ int op_units(const bigint_op &o) {
   const int a = std::min(o.na, 8192), b = std::min(o.nb, 8192);
   if (o.op == BIGINT_OP_MUL) return blk_mul_units<BRB, BQ>(a, b);
   if (o.op == BIGINT_OP_DIVMOD) return blk_mul_units<DRB, DQ>(a, a);
-  return std::min(o.na / 8 + 32, 512);
+  return std::min(std::max(o.na, o.nb) / 8 + 32, 512);
 }
 
 int threads_for_units(int units) {
@@ -343,7 +348,10 @@ int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out) {
     if (o.op < BIGINT_OP_ADD || o.op > BIGINT_OP_DIVMOD) return BIGINT_EINVAL;
     if (o.na < 1 || o.nb < 1 || o.na > BIGINT_MAX_LIMBS || o.nb > BIGINT_MAX_LIMBS)
       return BIGINT_EINVAL;
-    if ((o.op == BIGINT_OP_ADD || o.op == BIGINT_OP_SUB) && o.na != o.nb) return BIGINT_EINVAL;
+    if ((o.op == BIGINT_OP_ADD || o.op == BIGINT_OP_SUB) && o.na != o.nb &&
+        !(o.flags & BIGINT_ZEXT))
+      return BIGINT_EINVAL;
+    if (o.flags & ~BIGINT_ZEXT) return BIGINT_EINVAL;
     if (o.op == BIGINT_OP_MUL && (o.na > BIGINT_MUL_MAX_LIMBS || o.nb > BIGINT_MUL_MAX_LIMBS))
       return BIGINT_EINVAL;
     if (o.a < 0 || o.b < 0 || o.o1 < 0 || o.o2 < 0) return BIGINT_EINVAL;

@@ -219,7 +219,7 @@ def ragged_ops(seed: int, count: int, min_limbs: int = 512, max_limbs: int = 819
     bigint_op layout."""
     import numpy as np
 
-    dt = np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("reserved", "<i4"),
+    dt = np.dtype([("op", "<i4"), ("na", "<i4"), ("nb", "<i4"), ("flags", "<i4"),
                    ("a", "<i8"), ("b", "<i8"), ("o1", "<i8"), ("o2", "<i8")])
     n = ragged_sizes(seed, count, min_limbs=min_limbs, max_limbs=max_limbs)
     if min_limbs < 512 or max_limbs < 8192:  # small test batches: spread over the range

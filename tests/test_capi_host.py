@@ -163,3 +163,46 @@ def test_host_calls_check_arguments():
     assert lib.bigint_add_host(p, p, p, None, 2, 0, p, 1 << 20) == bi.EINVAL
     assert lib.bigint_divmod_host(p, p, p, None, None, 2, 4, 2, p, 1 << 20) == bi.EINVAL
     assert lib.bigint_divmod_host(p, p, p, p, None, -1, 4, 2, p, 1 << 20) == bi.EINVAL
+
+
+def test_views_rejected_on_the_host(L):
+    """Malformed views and mismatched lengths are refused before any device
+    work (no GPU needed)."""
+    import numpy as np
+
+    import paper_2607_28897_gb300 as bi
+
+    class V(ctypes.Structure):
+        _fields_ = [("data", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+                    ("nlimbs", ctypes.c_void_p), ("count", ctypes.c_int64), ("n", ctypes.c_int32)]
+
+    def v(count, n, data=256, lengths=None):
+        x = V()
+        x.data, x.count, x.n = data, count, n
+        if lengths is not None:
+            arr = np.asarray(lengths, dtype=np.int32)
+            off = np.arange(len(arr), dtype=np.int64) * 100
+            x.offset, x.nlimbs = off.ctypes.data, arr.ctypes.data
+            x._keep = (arr, off)
+        return x
+
+    a, b = v(4, 8), v(4, 8)
+    ws = ctypes.c_void_p(256)
+    for out, flags, why in ((v(4, 9), 0, "wrong result length"),
+                            (v(3, 8), 0, "count mismatch"),
+                            (v(4, 8, data=260), 0, "misaligned data"),
+                            (v(4, 8), 2, "unknown flag")):
+        assert L.bigint_batch_add(ctypes.byref(a), ctypes.byref(b), ctypes.byref(out), None, flags,
+                                  ws, 1 << 20, None) == bi.EINVAL, why
+    ragged = v(2, 0, lengths=[5, 7])
+    same = v(2, 0, lengths=[5, 5])
+    out7 = v(2, 0, lengths=[5, 7])
+    assert L.bigint_batch_sub(ctypes.byref(ragged), ctypes.byref(same), ctypes.byref(out7), None,
+                              0, ws, 1 << 20, None) == bi.EINVAL  # unequal without ZEXT
+    assert L.bigint_batch_mul(ctypes.byref(a), ctypes.byref(b), ctypes.byref(v(4, 15)), ws,
+                              1 << 20, None) == bi.EINVAL  # product needs 16 limbs
+    q, r = v(4, 1), v(4, 7)
+    assert L.bigint_batch_divmod(ctypes.byref(a), ctypes.byref(b), ctypes.byref(q),
+                                 ctypes.byref(r), None, ws, 1 << 20, None) == bi.EINVAL
+    assert L.bigint_batch_run(None, 3, None, None, None, ws, 0, 0, None) == bi.EINVAL
+    assert L.bigint_batch_run(None, 0, None, None, None, None, 0, 9, None) == bi.EINVAL
