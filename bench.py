@@ -461,7 +461,7 @@ def main():
         o1 = torch.empty((1, 2 * n), dtype=torch.int64, device=dev)
         ws1 = torch.empty(max(1, bi.mul_split_workspace_bytes(1, n, n)), dtype=torch.uint8,
                           device=dev)
-        row = {"tiles": bi.mul_split_workspace_bytes(1, n, n) // 16}
+        row = {"form": "split-K: (tile, group) units over the SMs, column sums added atomically"}
         for name, fn in (("mul_us", lambda: bi.mul(a1, b1, out=o1, stream=stream)),
                          ("mul_split_us", lambda: bi.mul_split(a1, b1, out=o1, workspace=ws1,
                                                                stream=stream))):
@@ -584,6 +584,10 @@ def main():
             serving = serving_block(torch, bi, [float(r) for r in args.rates.split(",")],
                                     args.serving_requests, 1000)
 
+    # ---- the autotuner against the built-in choice, on an eighth of each
+    #      sweep batch (the built-in table is restored afterwards)
+    tuning = tuning_block(torch, bi, sweep, sizes) if not args.no_forms else None
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,12 +603,75 @@ def main():
             "data": "synthetic", "config": workload_config(sizes), "roofline": roofline,
             "roofline_add": roofline_add, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "breakdown": breakdown,
-            "latency": latency, "batched": batched, "serving": serving,
+            "latency": latency, "batched": batched, "serving": serving, "tuning": tuning,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def tuning_block(torch, bi, sweep, sizes):
+    """bigint_tune on an eighth of each sweep batch: the variant it picks
+    against the built-in one, with the product's time under each."""
+    import tempfile
+
+    def best_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        out = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out = min(out, e0.elapsed_time(e1))
+        return out
+
+    res = {}
+    try:
+        for n in sizes:
+            k = max(1, sweep_batch(n) // 8)
+            a, b, p = sweep[n]["a"][:k], sweep[n]["b"][:k], sweep[n]["p"][:k]
+            v0 = bi.mul_variant_for(n, n)
+            t0 = best_ms(lambda: bi.mul(a, b, out=p))
+            v1 = bi.tune(a, b, out=p)
+            t1 = best_ms(lambda: bi.mul(a, b, out=p))
+            res[str(n)] = {"batch": k, "builtin_variant": v0, "builtin_ms": round(t0, 3),
+                           "tuned_variant": v1, "tuned_ms": round(t1, 3)}
+    finally:
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "t.json")
+            bi.save_tuning(path)
+            table = json.load(open(path))
+            table["mul_variant_by_class"] = [0] * 32
+            json.dump(table, open(path, "w"))
+            bi.load_tuning(path)
+    return res
+
+
+def bind_to_gpu_cpus(torch, dev):
+    """Restricts this process to the CPUs next to the GPU (the PCI device's
+    local_cpulist in sysfs), so that the pinned host buffers allocated
+    afterwards sit in the GPU's NUMA-local memory, as a deployment binds a
+    GPU's feeder process.  Returns what was done (or why not)."""
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        path = f"/sys/bus/pci/devices/{bus}/local_cpulist"
+        text = open(path).read().strip()
+        cpus = set()
+        for part in text.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return {"bound": False, "why": f"no usable CPU in {text}"}
+        os.sched_setaffinity(0, cpus)
+        return {"bound": True, "pci": bus, "cpus": text}
+    except (OSError, AttributeError, ValueError) as e:
+        return {"bound": False, "why": type(e).__name__}
 
 
 def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, world, dist):
@@ -616,6 +683,16 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     kernels of the next.  Timed on the host clock; calls_ms are enqueue
     times, "sync" the wait for the step's work."""
     steps = max(1, args.e2e_steps)
+    all_cpus = os.sched_getaffinity(0)
+    numa = bind_to_gpu_cpus(torch, dev)
+    try:
+        return _run_e2e(args, torch, bi, sweep, divs, sizes, dev, limb_ops_step, world, dist,
+                        steps, numa)
+    finally:  # the CPU baseline that follows uses every host core again
+        os.sched_setaffinity(0, all_cpus)
+
+
+def _run_e2e(args, torch, bi, sweep, divs, sizes, dev, limb_ops_step, world, dist, steps, numa):
 
     def pinned_like(t, dtype=None):
         return torch.empty(tuple(t.shape), dtype=dtype or t.dtype).pin_memory()
@@ -686,14 +763,14 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     probe_h = torch.empty(1 << 26, dtype=torch.int64).pin_memory()
     probe_d = torch.empty(1 << 26, dtype=torch.int64, device=dev)
 
-    def copy_gbs(fn):
+    def copy_gbs(fn, nbytes=probe_h.numel() * 8):
         fn()
         torch.cuda.synchronize()
         c0 = time.perf_counter()
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
-        return 3 * probe_h.numel() * 8 / (time.perf_counter() - c0) / 1e9
+        return 3 * nbytes / (time.perf_counter() - c0) / 1e9
 
     h2d_gbs = copy_gbs(lambda: probe_d.copy_(probe_h, non_blocking=True))
     d2h_gbs = copy_gbs(lambda: probe_h.copy_(probe_d, non_blocking=True))
@@ -711,6 +788,15 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
 
     both_gbs = 2 * copy_gbs(both)
     del probe_h, probe_d, probe_h2, probe_d2
+    # the same rates on the step's own largest pinned buffers (where they were
+    # placed can differ from a freshly pinned probe buffer)
+    nbig = max(sizes)
+    own_h, own_o = host_in[nbig][0], host_out[nbig][2]
+    own_d = torch.empty_like(sweep[nbig]["a"])
+    own_p = torch.empty_like(sweep[nbig]["p"])
+    own_h2d = copy_gbs(lambda: own_d.copy_(own_h, non_blocking=True), own_h.numel() * 8)
+    own_d2h = copy_gbs(lambda: own_o.copy_(own_p, non_blocking=True), own_o.numel() * 8)
+    del own_d, own_p
 
     step()
     torch.cuda.synchronize()
@@ -724,12 +810,14 @@ def run_e2e(args, torch, bi, sweep, divs, sizes, dev, stream, limb_ops_step, wor
     from paper_2607_28897_gb300 import ranks
 
     dt = ranks.max_over_ranks(time.perf_counter() - t0, dist, dev)
-    return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT,
+    return {"value": world * limb_ops_step * steps / dt / 1e9, "unit": UNIT, "host_binding": numa,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "path": "bigint_host_async + bigint_host_sync (C ABI, pinned host buffers, copies "
                     "overlapped with kernels)",
             "host_link_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1),
-                              "both_directions_at_once": round(both_gbs, 1)},
+                              "both_directions_at_once": round(both_gbs, 1),
+                              "h2d_step_buffer": round(own_h2d, 1),
+                              "d2h_step_buffer": round(own_d2h, 1)},
             "copy_bound_ms_per_step": round((h2d + d2h) / (both_gbs * 1e9) * 1e3, 1),
             "calls_ms": {k: round(v / steps, 2) for k, v in calls_ms.items()}}
 
@@ -894,7 +982,9 @@ def serving_block(torch, bi, rates, requests, per_request_sample):
     res = []
     for rate in rates:
         w = serve.make_workload(41, requests, rate)
-        serve.run_continuous(serve.make_workload(42, 200, rate))  # warm-up
+        # warm-up over the whole size range, so that the device and pinned
+        # host allocators have grown to the sizes the timed run asks for
+        serve.run_continuous(serve.make_workload(42, 2000, rate))
         c = serve.run_continuous(w)
         p = serve.run_per_request(w, limit=min(requests, per_request_sample))
         res.append({"rate": rate,

@@ -130,11 +130,18 @@ int get_pipe(Pipe **pp) {
   return BIGINT_OK;
 }
 
+// Divisions in chunks of fewer instances than this run each Newton step's
+// products on too few SMs (measured: 256 divisions of 2^20 by 2^19 bits in
+// four chunks of 64 took 9.7 ms through this path against 4.3 ms in one
+// launch), so a division chunk holds at least this many (or the batch).
+constexpr int64_t MIN_DIV_CHUNK = 1024;
+
 // Instances per chunk: what two slots of the workspace hold, and at most a
 // quarter of the batch (so that copies and kernels of different chunks
-// overlap), at least 1.
+// overlap) -- for divisions at least MIN_DIV_CHUNK -- at least 1.
 int64_t chunk_size(const Shape &s, int64_t count, size_t bytes) {
   int64_t hi = (count + 3) / 4;
+  if (s.op == BIGINT_OP_DIVMOD && hi < MIN_DIV_CHUNK) hi = count < MIN_DIV_CHUNK ? count : MIN_DIV_CHUNK;
   if (hi < 1) hi = 1;
   int64_t lo = 0;  // largest c with 2 slot_bytes(c) <= bytes
   int64_t a = 1, b = count;
