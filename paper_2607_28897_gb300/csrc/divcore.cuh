@@ -140,14 +140,39 @@ __device__ __noinline__ bool tc_call(tcm::TcCtx *c, const uint64_t *x, int nx, c
 // written) otherwise.  With lo > 0 the tensor-core band semantics apply
 // (tc_product): limbs >= lo + 2 are exact or one unit of limb lo + 2 high,
 // limbs below the first computed tile are not written.
+// Toeplitz blocks the 256-column tiles of x * y (x of nx limbs with its
+// carry digit) issue for the limbs [lo, nout), as tc_product's tile loop.
+__device__ __forceinline__ int tc_blocks256(int nx, int ny, int nout, int lo) {
+  const int mx = (8 * nx + 1 + 127) / 128, ey = (8 * ny + 127) / 128, ctot = mx + ey;
+  int blocks = 0;
+  for (int c0 = lo > 0 ? lo / 16 : 0; 16 * c0 < nout; c0 += 256) {
+    int W = ctot - c0 < 256 ? ctot - c0 : 256;
+    const int need = (nout - 16 * c0 + 15) / 16;
+    if (W > need) W = need;
+    W = (W + 15) & ~15;
+    const int e_lo = c0 - mx + 1 > 0 ? c0 - mx + 1 : 0, e_hi = c0 + W - 1 < ey ? c0 + W - 1 : ey;
+    if (e_hi >= e_lo) blocks += e_hi - e_lo + 1;
+  }
+  return blocks;
+}
+
 __device__ __forceinline__ bool tc_mul(tcm::TcCtx *tc, const uint64_t *x, int nx,
                                        const uint64_t *y, int ny, uint64_t *out, int nout,
                                        int smem_words, int lo) {
-  const int ns = nx < ny ? nx : ny, nl = nx < ny ? ny : nx;
+  int ns = nx < ny ? nx : ny, nl = nx < ny ? ny : nx;
   if (tc == nullptr || tc->aborted || ns < TC_DIV_MIN) return false;
   const uint64_t *xs = nx <= ny ? x : y, *ys = nx <= ny ? y : x;
   const int no = nout < nx + ny ? nout : nx + ny;
   const uint32_t bytes = 4u * (uint32_t)smem_words;
+  // the shorter operand as the Toeplitz side (y) where that issues fewer
+  // MMAs (a low product whose longer operand has most of the columns: an
+  // MMA narrower than ~136 columns costs its A operand's read, so fewer,
+  // wider MMAs win) and the longer one fits shared memory as x
+  if (ns != nl && tcm::layout<256, 4>(nl, ns).total <= bytes &&
+      tc_blocks256(nl, ns, no, lo) < tc_blocks256(ns, nl, no, lo)) {
+    const uint64_t *t = xs; xs = ys; ys = t;
+    const int tn = ns; ns = nl; nl = tn;
+  }
   if (tcm::layout<256, 8>(ns, nl).total <= bytes)
     tc_call<8>(tc, xs, ns, ys, nl, out, no, lo);
   else if (tcm::layout<256, 4>(ns, nl).total <= bytes)

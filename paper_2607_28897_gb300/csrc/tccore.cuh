@@ -528,9 +528,11 @@ __device__ void tc_release(TcCtx &c) {
 }
 
 // out[0..nout) = low nout limbs of x * y, by the whole CTA (blockDim = 2 NT,
-// plus one issuer warp when IW),
-// with nx <= ny, nout <= nx + ny, x, y, out in global memory (out disjoint
-// from x and y) and c.sm holding layout<NT, G>(nx, ny).total bytes.
+// plus one issuer warp when IW), with nout <= nx + ny, x, y, out in global
+// memory (out disjoint from x and y) and c.sm holding layout<NT, G>(nx,
+// ny).total bytes.  Either operand may be the longer one (x is stored whole
+// in shared memory, y is read group by group); the column sums stay below
+// 2^31 while the shorter operand has at most 16383 limbs.
 //
 // Band mode (lo > 0): the tiles start at the column that holds limb lo
 // (limb L0 = 16 floor(lo / 16) <= lo), so no column below it is computed;
