@@ -824,8 +824,10 @@ def _run_e2e(args, torch, bi, sweep, divs, sizes, dev, limb_ops_step, world, dis
 def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
     """The batched form: `count` ragged instances (sizes log-uniform over
     2^15..2^19 bits; 40 % mul, 15 % add, 15 % sub, 30 % divmod) in one
-    persistent launch with a device-side work queue (tuned CTA size,
-    CUDA-graph replay), against one launch per (op, size class).  With
+    persistent launch with a device-side work queue, in the steps form
+    (large divisions grouped into padded shape classes and divided
+    step-batched, the rest persistent), the faster of the two tuned and
+    replayed as a CUDA graph, against one launch per (op, size class).  With
     several ranks the batch is split by estimated cost (ranks.partition) and
     every rank runs its share (strong scaling of the fixed batch); times are
     the maximum over ranks."""
@@ -860,27 +862,33 @@ def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
     t_class = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PER_CLASS), reps)
     ref = out.clone()
     t_pers = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_PERSISTENT), reps)
-    same_pers = bool(torch.equal(out, ref))
+    same = bool(torch.equal(out, ref))
+    t_steps = best_of(lambda: B.launch(pool, out, st, mode=bi.BATCH_STEPS), reps)
+    same = same and bool(torch.equal(out, ref))
     threads = B.tune(pool, out, st)
+    # the faster of the persistent and the steps form, tuned, as a CUDA graph
+    mode = bi.BATCH_STEPS if t_steps < t_pers else bi.BATCH_PERSISTENT
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
-        B.launch(pool, out, st, stream=s)
+        B.launch(pool, out, st, mode=mode, stream=s)
         torch.cuda.synchronize()
         with torch.cuda.graph(g, stream=s):
-            B.launch(pool, out, st, stream=s)
+            B.launch(pool, out, st, mode=mode, stream=s)
     t_graph = best_of(lambda: g.replay(), reps)
-    same = same_pers and bool(torch.equal(out, ref))
+    same = same and bool(torch.equal(out, ref))
     bad_status = int((st[:len(ops)] < 0).sum().item()) if len(ops) else 0
     del pool, out, st, ref, g
     B.close()
     torch.cuda.empty_cache()
-    best = min(t_pers, t_graph)
+    best = min(t_pers, t_steps, t_graph)
     return {"workload": f"{count} ragged instances, 2^15..2^19 bits log-uniform, 40% mul / 15% "
                         "add / 15% sub / 30% divmod (n_u in [n_v, 2 n_v])",
             "ops_per_s": count / (best * 1e-3), "per_class_ms": t_class,
-            "persistent_ms": t_pers, "persistent_tuned_graph_ms": t_graph,
+            "persistent_ms": t_pers, "steps_ms": t_steps,
+            "graph_form": "steps" if mode == bi.BATCH_STEPS else "persistent",
+            "tuned_graph_ms": t_graph,
             "tuned_threads": threads, "speedup_vs_per_class": t_class / best,
             "results_identical_across_forms": same, "negative_statuses": bad_status,
             "scaling": "strong" if world > 1 else None,

@@ -136,9 +136,9 @@ int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out,
  * Schedule: with divisors of 128 limbs or more (and nu >= nv) every Newton
  * step runs for all instances at once -- each product one batched launch
  * of the multiply kernels, each linear step one small launch -- and only
- * instances whose dividend or divisor has a zero top limb are divided one
- * CTA each at the end; smaller divisions run one CTA per division (the
- * paper's intragroup form).  Results are the same either way.             */
+ * instances whose divisor has a zero top limb are divided one CTA each at
+ * the end; smaller divisions run one CTA per division (the paper's
+ * intragroup form).  Results are the same either way.                     */
 int bigint_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q,
                   uint64_t *r, int32_t *status, int64_t count, int32_t nu,
                   int32_t nv, void *workspace, size_t workspace_bytes,
@@ -228,9 +228,18 @@ typedef struct {
 } bigint_op;
 
 /* Launch forms: one persistent launch with a device-side work queue
- * (cost-sorted, largest first), or one launch per (op, size class). */
+ * (cost-sorted, largest first); one launch per (op, size class); or the
+ * steps form: the divisions with divisors of 128 limbs or more grouped into
+ * classes of nearby shapes (divisors within 1/8, quotients within 1/4 plus
+ * 64 limbs, at least 8 members), each class padded to one shape (u and v
+ * shifted up by the same number of zero limbs: the quotient is the same,
+ * the remainder comes back shifted down) and divided in the step-batched
+ * form of bigint_divmod, everything else in one persistent launch.  All
+ * forms are device work only (a CUDA graph can capture them) and give the
+ * same results. */
 #define BIGINT_BATCH_PERSISTENT 0
 #define BIGINT_BATCH_PER_CLASS 1
+#define BIGINT_BATCH_STEPS 2
 
 typedef struct bigint_batch bigint_batch; /* opaque host-side plan */
 

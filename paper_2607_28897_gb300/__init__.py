@@ -27,7 +27,7 @@ __all__ = [
 
 OK, EINVAL, EDIVZERO, ENOMEM, ETIMEOUT, EINTERNAL, ECUDA, ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
 OP_ADD, OP_SUB, OP_MUL, OP_DIVMOD = 1, 2, 3, 4
-BATCH_PERSISTENT, BATCH_PER_CLASS = 0, 1
+BATCH_PERSISTENT, BATCH_PER_CLASS, BATCH_STEPS = 0, 1, 2
 MAX_LIMBS = 16384
 MUL_MAX_LIMBS = 10000
 

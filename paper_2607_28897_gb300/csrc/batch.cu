@@ -209,6 +209,54 @@ int batch_set_threads(int t) {
 }
 int batch_get_threads() { return g_batch_threads; }
 
+// A class of divisions of nearby shapes run together in the step-batched
+// form: every member u (nu limbs) / v (nv limbs) is padded to u' = u B^s
+// (H limbs) and v' = v B^s (NV limbs), s = NV - nv, so floor(u'/v') =
+// floor(u/v) and u' mod v' = (u mod v) B^s (same quotient, the remainder
+// shifted by s limbs); the quotient has LQ = H - NV + 1 limbs.
+struct DivClass {
+  int H, NV, LQ, first, count;
+};
+
+// One CTA per member of a class: the padded operands.
+__global__ void __launch_bounds__(256)
+    k_cls_gather(const OpDev *__restrict__ ops, const int32_t *__restrict__ order, int first,
+                 const uint64_t *__restrict__ in, uint64_t *Uc, uint64_t *Vc, int H, int NV) {
+  const OpDev o = ops[order[first + blockIdx.x]];
+  const int s = NV - o.nb;
+  const uint64_t *a = in + o.a, *b = in + o.b;
+  uint64_t *u = Uc + (int64_t)blockIdx.x * H, *v = Vc + (int64_t)blockIdx.x * NV;
+  for (int j = threadIdx.x; j < H; j += blockDim.x)
+    u[j] = (j >= s && j - s < o.na) ? a[j - s] : 0ull;
+  for (int j = threadIdx.x; j < NV; j += blockDim.x) v[j] = j >= s ? b[j - s] : 0ull;
+}
+
+// One CTA per member: q (its max(nu - nv + 1, 1) limbs) and r (nv limbs,
+// the padded remainder shifted back by s) into the output pool; status
+// BIGINT_ERANGE where the quotient does not fit its limbs (a divisor with
+// zero top limbs), else the class division's status.
+__global__ void __launch_bounds__(256)
+    k_cls_scatter(const OpDev *__restrict__ ops, const int32_t *__restrict__ order, int first,
+                  const uint64_t *__restrict__ Qc, const uint64_t *__restrict__ Rc,
+                  const int32_t *__restrict__ stc, uint64_t *out, int32_t *status, int LQ, int NV) {
+  const int opi = order[first + blockIdx.x];
+  const OpDev o = ops[opi];
+  const int s = NV - o.nb, nq = o.na - o.nb + 1 > 1 ? o.na - o.nb + 1 : 1;
+  const uint64_t *q = Qc + (int64_t)blockIdx.x * LQ, *r = Rc + (int64_t)blockIdx.x * NV;
+  int high = 0;
+  for (int j = threadIdx.x; j < LQ; j += blockDim.x) {
+    if (j < nq) out[o.o1 + j] = q[j];
+    else if (q[j] != 0) high = 1;
+  }
+  for (int j = threadIdx.x; j < o.nb; j += blockDim.x) out[o.o2 + j] = r[s + j];
+  high = __syncthreads_or(high);
+  if (status != nullptr && threadIdx.x == 0) {
+    int st = stc[blockIdx.x];
+    if (st == BIGINT_OK && high) st = BIGINT_ERANGE;
+    status[opi] = st;
+  }
+}
+
 }  // namespace bigint
 
 // The opaque batch handle of include/bigint.h.
@@ -218,9 +266,15 @@ struct bigint_batch {
   std::vector<int32_t> order_classes;     // grouped by (op, size class)
   std::vector<bigint::Launch> classes;    // one launch per class
   bigint::Launch persistent;
+  // BIGINT_BATCH_STEPS: divisions grouped into shape classes (each run
+  // step-batched on padded operands), the other operations persistent
+  std::vector<int32_t> order_rest;        // order_persistent without the class divisions
+  std::vector<int32_t> order_div;         // the class divisions, class by class
+  std::vector<bigint::DivClass> div_classes;
   int64_t ws_limbs_per_cta = 0;
   int max_ctas = 0;
   size_t desc_off = 0, order_p_off = 0, order_c_off = 0, queue_off = 0, scratch_off = 0;
+  size_t order_r_off = 0, order_d_off = 0, cls_off = 0, cls_ws_off = 0, cls_ws_bytes = 0;
   size_t workspace_bytes = 0;
   int sms = 0, optin = 0;
   int threads_override = 0;  // set by the tuner for this batch
@@ -262,6 +316,70 @@ int occupancy(bool tc, int threads, int smem_words, int *per_sm) {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t divmod_workspace(int64_t count, int nu, int nv);
+
+namespace {
+
+// Divisions with divisors of at least this many limbs join shape classes.
+constexpr int CLS_MIN_NV = 128;
+// A class keeps divisors within 1/8 and quotient lengths within 1/4 (plus
+// 64 limbs) of its smallest, and has at least CLS_MIN_COUNT members (fewer
+// stay with the persistent launch: a class costs some 50 small launches).
+constexpr int CLS_MIN_COUNT = 8;
+
+// Groups the batch's large divisions into classes of nearby shapes and
+// orders the other operations for the persistent launch of the steps form.
+void plan_div_classes(bigint_batch *B) {
+  B->order_div.clear();
+  B->div_classes.clear();
+  std::vector<int32_t> cand;
+  for (int32_t i = 0; i < (int32_t)B->ops.size(); i++) {
+    const bigint_op &o = B->ops[i];
+    if (o.op == BIGINT_OP_DIVMOD && o.nb >= CLS_MIN_NV && o.na >= o.nb) cand.push_back(i);
+  }
+  auto L = [&](int32_t i) { return B->ops[i].na - B->ops[i].nb + 1; };
+  std::stable_sort(cand.begin(), cand.end(),
+                   [&](int32_t x, int32_t y) { return B->ops[x].nb < B->ops[y].nb; });
+  std::vector<char> in_class(B->ops.size(), 0);
+  for (size_t i = 0; i < cand.size();) {
+    const int nv0 = B->ops[cand[i]].nb;
+    size_t j = i;
+    while (j < cand.size() && (int64_t)B->ops[cand[j]].nb * 8 <= (int64_t)nv0 * 9) j++;
+    std::stable_sort(cand.begin() + i, cand.begin() + j,
+                     [&](int32_t x, int32_t y) { return L(x) < L(y); });
+    for (size_t a = i; a < j;) {
+      const int l0 = L(cand[a]);
+      size_t b = a;
+      int nv = 0, lq = 0;
+      while (b < j && (int64_t)L(cand[b]) * 4 <= (int64_t)l0 * 5 + 256) {
+        nv = std::max(nv, (int)B->ops[cand[b]].nb);
+        lq = std::max(lq, L(cand[b]));
+        b++;
+      }
+      if (b - a >= (size_t)CLS_MIN_COUNT) {
+        DivClass c;
+        c.NV = nv;
+        c.LQ = lq;
+        c.H = nv + lq - 1;
+        c.first = (int)B->order_div.size();
+        c.count = (int)(b - a);
+        for (size_t k = a; k < b; k++) {
+          B->order_div.push_back(cand[k]);
+          in_class[cand[k]] = 1;
+        }
+        B->div_classes.push_back(c);
+      }
+      a = b;
+    }
+    i = j;
+  }
+  B->order_rest.clear();
+  for (int32_t i : B->order_persistent)
+    if (!in_class[i]) B->order_rest.push_back(i);
+}
 
 }  // namespace
 
@@ -337,9 +455,29 @@ int batch_configure(bigint_batch *B) {
   B->order_c_off = B->order_p_off + align256(n * 4);
   B->queue_off = B->order_c_off + align256(n * 4);
   B->scratch_off = B->queue_off + 256;
-  B->workspace_bytes = B->scratch_off + (size_t)B->max_ctas * B->ws_limbs_per_cta * 8;
+  // the steps form: the rest's order, the class divisions' order, then one
+  // set of padded operands / results / statuses and one division workspace,
+  // sized for the largest class (the classes run one after the other)
+  B->order_r_off = B->scratch_off + align256((size_t)B->max_ctas * B->ws_limbs_per_cta * 8);
+  B->order_d_off = B->order_r_off + align256(B->order_rest.size() * 4);
+  B->cls_off = B->order_d_off + align256(B->order_div.size() * 4);
+  size_t cls = 0, cls_ws = 0;
+  for (const DivClass &c : B->div_classes) {
+    const size_t cnt = (size_t)c.count;
+    cls = std::max(cls, align256(8 * cnt * c.H) + align256(8 * cnt * c.NV) +
+                            align256(8 * cnt * c.LQ) + align256(8 * cnt * c.NV) +
+                            align256(4 * cnt));
+    cls_ws = std::max(cls_ws, divmod_workspace(c.count, c.H, c.NV));
+  }
+  B->cls_ws_off = B->cls_off + cls;
+  B->cls_ws_bytes = cls_ws;
+  B->workspace_bytes = B->div_classes.empty() ? B->order_d_off : B->cls_ws_off + cls_ws;
   return BIGINT_OK;
 }
+
+int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r,
+                  int32_t *status, int64_t count, int nu, int nv, void *ws, size_t ws_bytes,
+                  cudaStream_t st);
 
 int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out) {
   if (!out || nops < 0 || nops > 0x7fffffff || (nops > 0 && !ops)) return BIGINT_EINVAL;
@@ -378,6 +516,7 @@ int batch_create(const bigint_op *ops, int64_t nops, bigint_batch **out) {
   });
   for (const bigint_op &o : B->ops)
     if (o.op == BIGINT_OP_DIVMOD) B->ws_limbs_per_cta = std::max(B->ws_limbs_per_cta, ws_limbs(o.na, o.nb, o.na));
+  plan_div_classes(B);
   const int rc = batch_configure(B);
   if (rc != BIGINT_OK) {
     delete B;
@@ -399,6 +538,12 @@ int batch_upload(bigint_batch *B, void *ws, size_t bytes, cudaStream_t st) {
                                   cudaMemcpyHostToDevice, st));
   BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->order_c_off, B->order_classes.data(), n * 4,
                                   cudaMemcpyHostToDevice, st));
+  if (!B->order_rest.empty())
+    BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->order_r_off, B->order_rest.data(),
+                                    B->order_rest.size() * 4, cudaMemcpyHostToDevice, st));
+  if (!B->order_div.empty())
+    BIGINT_CUDA_TRY(cudaMemcpyAsync(w + B->order_d_off, B->order_div.data(),
+                                    B->order_div.size() * 4, cudaMemcpyHostToDevice, st));
   return BIGINT_OK;
 }
 
@@ -418,6 +563,45 @@ int batch_launch(const bigint_batch *B, const uint64_t *in, uint64_t *out, int32
         ops, reinterpret_cast<const int32_t *>(w + B->order_p_off), 0, P.count, in, out, status,
         scratch, B->ws_limbs_per_cta, queue, P.smem_words);
     return bigint_launch_status();
+  }
+  if (mode == BIGINT_BATCH_STEPS) {
+    // the operations outside the division classes: one persistent launch
+    const Launch &P = B->persistent;
+    const int nrest = (int)B->order_rest.size();
+    if (nrest > 0) {
+      int *queue = reinterpret_cast<int *>(w + B->queue_off);
+      BIGINT_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(int), st));
+      auto *kern = P.tc ? k_batch<true> : k_batch<false>;
+      kern<<<std::min(P.ctas, nrest), P.threads, (size_t)P.smem_words * 4, st>>>(
+          ops, reinterpret_cast<const int32_t *>(w + B->order_r_off), 0, nrest, in, out, status,
+          scratch, B->ws_limbs_per_cta, queue, P.smem_words);
+      const int rc = bigint_launch_status();
+      if (rc != BIGINT_OK) return rc;
+    }
+    // each class of divisions: padded operands, the step-batched division,
+    // results back into the pool
+    const int32_t *order_d = reinterpret_cast<const int32_t *>(w + B->order_d_off);
+    for (const DivClass &c : B->div_classes) {
+      const size_t cnt = (size_t)c.count;
+      char *p = w + B->cls_off;
+      uint64_t *Uc = reinterpret_cast<uint64_t *>(p); p += align256(8 * cnt * c.H);
+      uint64_t *Vc = reinterpret_cast<uint64_t *>(p); p += align256(8 * cnt * c.NV);
+      uint64_t *Qc = reinterpret_cast<uint64_t *>(p); p += align256(8 * cnt * c.LQ);
+      uint64_t *Rc = reinterpret_cast<uint64_t *>(p); p += align256(8 * cnt * c.NV);
+      int32_t *stc = reinterpret_cast<int32_t *>(p);
+      k_cls_gather<<<(unsigned)c.count, 256, 0, st>>>(ops, order_d, c.first, in, Uc, Vc, c.H,
+                                                        c.NV);
+      int rc = bigint_launch_status();
+      if (rc != BIGINT_OK) return rc;
+      rc = launch_divmod(Uc, Vc, Qc, Rc, stc, c.count, c.H, c.NV, w + B->cls_ws_off,
+                         B->cls_ws_bytes, st);
+      if (rc != BIGINT_OK) return rc;
+      k_cls_scatter<<<(unsigned)c.count, 256, 0, st>>>(ops, order_d, c.first, Qc, Rc, stc, out,
+                                                         status, c.LQ, c.NV);
+      rc = bigint_launch_status();
+      if (rc != BIGINT_OK) return rc;
+    }
+    return BIGINT_OK;
   }
   if (mode != BIGINT_BATCH_PER_CLASS) return BIGINT_EINVAL;
   for (const Launch &L : B->classes) {

@@ -13,12 +13,12 @@
 // arithmetic is that of divmod.cu; only the schedule differs.
 //
 // Every instance of a batch has the same shape (nu, nv), and for the usual
-// operands (top limbs of u and v nonzero, "regular") the same precisions
-// k = nv - 1 and h = nu, so the Newton schedule (l, m, t per step) is known
-// on the host.  Instances whose top limb of u or v is zero (including v = 0)
-// take the one-CTA-per-division kernel in a last launch; the step kernels
-// run over them too (their values are never used, and every size is fixed,
-// so nothing reads out of bounds).
+// operands (top limb of v nonzero, "regular") the same precision k = nv - 1
+// and the exponent h = nu, so the Newton schedule (l, m, t per step) is
+// known on the host.  Instances whose divisor has a zero top limb
+// (including v = 0) take the one-CTA-per-division kernel in a last launch;
+// the step kernels run over them too (their values are never used, and
+// every size is fixed, so nothing reads out of bounds).
 //
 // Per step, with the iterate w ~ B^(k+l) / v kept to l + 2 limbs,
 // m = min(l - 2, L - l), t = min(k, l + m + 2), vt = top t + 1 limbs of v:
@@ -57,8 +57,15 @@ constexpr int LIN_THREADS = 256;  // CTA of the linear per-instance kernels
 // integer pipes for 4096 instances.
 constexpr int STEP_TC_MIN = 64;
 
-__device__ __forceinline__ bool regular(const uint64_t *u, int nu, const uint64_t *v, int nv) {
-  return v[nv - 1] != 0 && u[nu - 1] != 0;
+// The step schedule needs k = prec(v) - 1 = nv - 1.  The dividend may have
+// leading zero limbs: with h = nu (not prec(u)) w ~ B^h / v still bounds the
+// quotient estimate u w / B^h within a few units of u / v since u < B^h,
+// and the banded u w + B^h < B^(nu + nw) still holds, so such instances
+// (the zero-padded operands of the batched form's division classes, or a
+// short dividend) stay on the step path at the cost of the product work
+// above their precision.
+__device__ __forceinline__ bool regular(const uint64_t *, int, const uint64_t *v, int nv) {
+  return v[nv - 1] != 0;
 }
 
 // One thread per instance: lists the irregular instances and writes the

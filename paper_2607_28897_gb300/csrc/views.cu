@@ -200,7 +200,9 @@ int bigint_batch_run(const bigint_op *ops, int64_t nops, const uint64_t *in_pool
                      uint64_t *out_pool, int32_t *status, void *workspace, size_t bytes, int mode,
                      void *stream) {
   if (nops < 0 || (nops > 0 && (!ops || !in_pool || !out_pool))) return BIGINT_EINVAL;
-  if (mode != BIGINT_BATCH_PERSISTENT && mode != BIGINT_BATCH_PER_CLASS) return BIGINT_EINVAL;
+  if (mode != BIGINT_BATCH_PERSISTENT && mode != BIGINT_BATCH_PER_CLASS &&
+      mode != BIGINT_BATCH_STEPS)
+    return BIGINT_EINVAL;
   return run_ops(std::vector<bigint_op>(ops, ops + nops), in_pool, out_pool, status, workspace,
                  bytes, mode, reinterpret_cast<cudaStream_t>(stream));
 }

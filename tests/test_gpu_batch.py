@@ -49,7 +49,7 @@ def check(ops, got_pool, got_st, exp, exp_st):
             assert np.array_equal(got_pool[o["o1"]:o["o1"] + r.size], r), i
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_small_ragged(orc, mode):
     import torch
 
@@ -192,11 +192,12 @@ def config4_slice(count, seed_ops=4, seed_pool=5):
     return np.concatenate([ops, extra]), np.concatenate(parts), opos
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_config4_slice_against_oracle(orc, mode):
     """A slice of the batched workload at its own sizes (up to 8192-limb
     products and 16384 / 8192-limb divisions on the tensor cores), in the
-    persistent and the per-class form, against the oracle op by op."""
+    persistent, the per-class and the steps form (division classes padded to
+    one shape and divided step-batched), against the oracle op by op."""
     import torch
 
     import paper_2607_28897_gb300 as bi
@@ -212,3 +213,52 @@ def test_batch_config4_slice_against_oracle(orc, mode):
     torch.cuda.synchronize()
     bi.check_timeout()
     check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
+
+
+def test_division_classes_with_irregular_members(orc):
+    """One class of divisions of nearby shapes (the steps form pads them to
+    one shape) whose members include a zero divisor, divisors with zero top
+    limbs (a quotient that may not fit), dividends with leading zero limbs
+    and a dividend below the divisor: the steps form equals the persistent
+    form and the oracle, statuses included."""
+    import torch
+
+    import paper_2607_28897_gb300 as bi
+    from paper_2607_28897_gb300 import inputs
+
+    rng = np.random.default_rng(81)
+    count = 40
+    nv = rng.integers(300, 330, count)
+    nu = nv + rng.integers(180, 220, count)
+    ops = np.zeros(count, dtype=bi.op_dtype())
+    ops["op"], ops["na"], ops["nb"] = bi.OP_DIVMOD, nu, nv
+    pos, opos, parts = 0, 0, []
+    for i in range(count):
+        a = inputs.limbs(500 + i, 1, int(nu[i]), top_nonzero=True)[0]
+        b = inputs.limbs(600 + i, 1, int(nv[i]), top_nonzero=True)[0]
+        if i == 0:
+            b[:] = 0                        # division by zero
+        elif i in (1, 2):
+            b[-3:] = 0                      # divisor with zero top limbs
+        elif i in (3, 4):
+            a[-50:] = 0                     # dividend with leading zero limbs
+        elif i == 5:
+            a[:] = 0
+            a[:10] = 7                      # dividend below the divisor
+        nq = int(nu[i] - nv[i] + 1)
+        ops[i]["a"], ops[i]["b"], ops[i]["o1"], ops[i]["o2"] = pos, pos + nu[i], opos, opos + nq
+        parts += [a, b]
+        pos += int(nu[i] + nv[i])
+        opos += nq + int(nv[i])
+    pool = np.concatenate(parts)
+    exp, exp_st = oracle_results(orc, ops, pool)
+    dpool = to_dev(pool).view(-1)
+    got = []
+    for mode in (0, 2):
+        dout = torch.zeros(opos, dtype=torch.int64, device="cuda")
+        st = torch.zeros(count, dtype=torch.int32, device="cuda")
+        bi.Batch(ops).launch(dpool, dout, st, mode=mode)
+        torch.cuda.synchronize()
+        check(ops, to_host(dout), st.cpu().numpy(), exp, exp_st)
+        got.append(to_host(dout))
+    assert np.array_equal(got[0], got[1])
