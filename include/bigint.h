@@ -440,11 +440,15 @@ int bigint_host_sync(void);
  *   variant 12: the tensor-core product -- the digit convolution of the
  *   schoolbook product (Sec. V-B) as fp16 matrix products (tcgen05.mma)
  *   over signed base-256 digits with exact fp32 accumulation -- with its
- *   tile chosen by the columns the product has; bit-identical results.
- *   Needs the shorter operand to fit shared memory (about 10700 limbs;
- *   otherwise variant 8).
- *   variants 13, 14, 15: variant 12 with tiles of 64, 128, 256 output
- *   columns (three, two, one CTAs per SM)
+ *   tile chosen by a cost model of its MMAs; bit-identical results.  Needs the shorter operand to fit shared memory
+ *   (about 10700 limbs; otherwise variant 8).
+ *   variants 13, 14, 15: variant 12 with 128-digit x blocks and tiles of
+ *   64, 128, 256 output columns (three, two, one CTAs per SM)
+ *   variants 16, 17: variant 12 with x blocks of 64 or 32 digits (128-column
+ *   tiles, two CTAs per SM: each MMA 2 or 4 times as wide)
+ *   Variants 13-17 also force the shape of the tensor-core products inside
+ *   divisions (where a forced shape cannot take a product, the model's
+ *   choice runs); variants 8-10 keep those on the integer pipes.
  * op 1 = division (divmod, shinv, divmod_inv):
  *   variant 0 (default): bigint_divmod on divisors of 128 limbs or more in
  *   the step-batched form (see bigint_divmod), everything else as variant 1

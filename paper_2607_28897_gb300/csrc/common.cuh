@@ -82,6 +82,12 @@ __device__ __forceinline__ void st_stream2(uint64_t *p, ulonglong2 v) {
 namespace bigint {
 // Counts the kernel launches the library enqueues (bigint_kernel_launches).
 void count_launch();
+
+// Shapes the tensor-core product can be forced to (the autotuner's
+// candidates; 0 = chosen by the cost model): 128-digit x blocks with the
+// 64-, 128- or 256-column tile, or narrow x blocks of 64 or 32 digits.
+constexpr int TC_FORCE_64 = 64, TC_FORCE_128 = 128, TC_FORCE_256 = 256;
+constexpr int TC_FORCE_N64 = 1064, TC_FORCE_N32 = 1032;
 }  // namespace bigint
 
 // Called right after every kernel launch of the library: counts it and

@@ -128,7 +128,7 @@ int mul_size_class(int na, int nb) {
 }
 
 bool mul_variant_valid(int v) {
-  return v == 0 || v == 8 || v == 9 || v == 10 || (v >= 12 && v <= 15);
+  return v == 0 || v == 8 || v == 9 || v == 10 || (v >= 12 && v <= 17);
 }
 
 int mul_set_variant(int v) {
@@ -162,9 +162,11 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
   const int v = mul_variant_for(na, nb, nout);
   switch (v) {
     case 12: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 0);
-    case 13: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 64);
-    case 14: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 128);
-    case 15: return launch_mul_tc(a, b, out, count, na, nb, nout, st, 256);
+    case 13: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_64);
+    case 14: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_128);
+    case 15: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_256);
+    case 16: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_N64);
+    case 17: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_N32);
     case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
     case 9: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
     default: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);
@@ -181,19 +183,27 @@ int launch_mul_tc_sk(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
                      int64_t so, int64_t count, int na, int nb, int nout, int lo, void *colsum,
                      size_t colsum_bytes, int *abort_flag, cudaStream_t st);
 
+// The products inside divisions and programs: variant 0 or 12 runs the
+// tensor-core product with its shape by the cost model (split-K for a few
+// products), variants 13-17 force its shape as for launch_mul, and variants
+// 8-10 keep them on the integer pipes.
 int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                   int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
                   cudaStream_t st, int tc_min, void *sk_ws, size_t sk_bytes) {
   if (count == 0) return BIGINT_OK;
   const int nmin = na < nb ? na : nb;
-  if (g_mul_variant == 0 || g_mul_variant == 12) {
+  const int v = g_mul_variant;
+  if (v == 0 || (v >= 12 && v <= 17)) {
     if (nmin >= tc_min && mul_tc_smem(na, nb) > 0) {
       // few products: cut each into units over the SMs (split-K)
-      if (sk_ws != nullptr && mul_sk_worth(count, na, nb, nout, lo) &&
+      if (v <= 12 && sk_ws != nullptr && mul_sk_worth(count, na, nb, nout, lo) &&
           sk_bytes >= (size_t)count * mul_sk_bytes_per_product(na, nb, nout, lo))
         return launch_mul_tc_sk(a, sa, b, sb, out, so, count, na, nb, nout, lo, sk_ws, sk_bytes,
                                 abort_flag, st);
-      return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st, 0);
+      static const int force[6] = {0, TC_FORCE_64, TC_FORCE_128, TC_FORCE_256, TC_FORCE_N64,
+                                   TC_FORCE_N32};
+      return launch_mul_tc_ex(a, sa, b, sb, out, so, count, na, nb, nout, lo, abort_flag, st,
+                              v <= 12 ? 0 : force[v - 12]);
     }
   }
   const int nmax = na > nb ? na : nb;

@@ -77,9 +77,10 @@
 namespace bigint {
 namespace tcm {
 
-// G: Toeplitz blocks per accumulation group; a group's Hankel buffer holds
-// 16 G + 15 core matrices.
-__host__ __device__ constexpr int hankel_blocks(int G) { return 16 * G + 15; }
+// G: Toeplitz blocks per accumulation group; KB: digits per x block (the
+// K of one Toeplitz block).  A group's Hankel buffer holds 16 G + KB / 8 - 1
+// core matrices.
+__host__ __device__ constexpr int hankel_blocks(int G, int KB = 128) { return 16 * G + KB / 8 - 1; }
 constexpr int ZB = 18;           // zero core matrices (operand of the clearing MMA)
 // NT: output columns per tile (= MMA N at most); 2 NT threads, 2 NT TMEM
 // columns (two accumulators).
@@ -108,9 +109,9 @@ static __device__ long long g_wait_limit = WAIT_LIMIT;
 static __device__ int g_never_set = 0;
 
 struct Layout {
-  int mx;    // x blocks of 128 digits (8 nx digits, + the carry digit if XC)
+  int mx;    // x blocks of KB digits (8 nx digits, + the carry digit if XC)
   int ey;    // last Toeplitz block index of y (e in [0, ey])
-  int ctot;  // output columns with nonzero coefficients: mx + ey
+  int ctot;  // output columns with nonzero coefficients: mx + S ey + S - 1 (S = 128 / KB)
   int ptot;  // stored x blocks (16 zero blocks on each side; odd)
   // byte offsets in dynamic shared memory: x (B layout), zero core matrices,
   // the two Hankel buffers, the column-sum transpose area (also the Hankel
@@ -118,21 +119,31 @@ struct Layout {
   uint32_t xs, z, h0, h1, cs, his, total;
 };
 
-template <int NT, int G, bool XC = true>
+// KB = 128: one output column per 128 digits, each coefficient in one TMEM
+// row.  KB = 64 or 32 (narrow x blocks): columns of KB digits whose 128-row
+// windows overlap, S = 128 / KB rows per coefficient (below).  Shared memory:
+// x, the zero core matrices, two Hankel buffers, the column-sum transpose
+// area (32 columns, then S - 1 columns carried from the previous 32), the
+// high words of the tile's limbs.
+template <int NT, int G, bool XC = true, int KB = 128>
 __host__ __device__ inline Layout layout(int nx, int ny) {
-  constexpr int HB = hankel_blocks(G);
+  static_assert(KB == 128 || KB == 64 || KB == 32, "x blocks of 128, 64 or 32 digits");
+  constexpr int HB = hankel_blocks(G, KB), S = 128 / KB, R = KB / 8;
   Layout L;
-  L.mx = (8 * nx + (XC ? 1 : 0) + 127) / 128;
-  L.ey = (8 * ny + 127) / 128;  // block e meets y digits 128 e - 127 .. 128 e + 127
-  L.ctot = L.mx + L.ey;
-  L.ptot = (L.mx + 32) | 1;  // odd: the 16 h-rows of a warp's x stores hit distinct banks
+  L.mx = (8 * nx + (XC ? 1 : 0) + KB - 1) / KB;
+  // block e meets y digits 128 e - KB + 1 .. 128 e + 127
+  L.ey = (8 * ny + KB - 1) / 128;
+  // the MMAs write columns up to mx - 1 + S ey; the rows of the last ones
+  // reach S - 1 columns further
+  L.ctot = L.mx + S * L.ey + S - 1;
+  L.ptot = (L.mx + 32) | 1;  // odd: the h-rows of a warp's x stores hit distinct banks
   L.xs = 0;
-  L.z = (uint32_t)L.ptot * 256u;
+  L.z = (uint32_t)L.ptot * 16u * R;
   L.h0 = L.z + ZB * 128;
   L.h1 = L.h0 + HB * 128;
   L.cs = L.h1 + HB * 128;
-  L.his = L.cs + 32 * 128 * 4;
-  L.total = L.his + NT * 16 * 4;
+  L.his = L.cs + (32 + S - 1) * 128 * 4;
+  L.total = L.his + NT * R * 4;
   return L;
 }
 
@@ -259,6 +270,17 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Asks L2 for the 16-byte-aligned part of [p, p + bytes) (no completion to
+// wait for): the next instance's operands come in from HBM while this one
+// is computed, so its first loads meet L2 rather than HBM.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a))
+                 : "memory");
+}
+
 // ---- digits ----------------------------------------------------------------
 // Recoded digit k of a limb (k = 0..7): its byte k sign-extended plus the top
 // bit of byte k - 1 (byte -1 = the top byte of the limb below), so a number
@@ -298,29 +320,29 @@ __device__ __forceinline__ uint32_t unbias_h2(uint32_t m) {
   return *reinterpret_cast<const uint32_t *>(&r);
 }
 
-// x blocks p in [-16, mx + 16) into the B layout: chunk (p, h) = digits
-// 128 p + 8 h .. + 8 = the digits of limb 16 p + h, stored at
-// ((p + 16) + h ptot) * 16.  Without XC the digits past limb nx - 1 are 0
-// (they spell x - top_bit(x) B^nx).  Thread i takes limb i - 256, so a
-// warp's loads are coalesced; a thread issues the loads of four limbs before
-// it recodes any, so their latencies overlap.
-template <bool XC>
+// x blocks p in [-16, mx + 16) into the B layout: with R = KB / 8 limbs per
+// block, chunk (p, h) = digits KB p + 8 h .. + 8 = the digits of limb R p +
+// h, stored at ((p + 16) + h ptot) * 16.  Without XC the digits past limb
+// nx - 1 are 0 (they spell x - top_bit(x) B^nx).  Thread i takes limb
+// i - 16 R, so a warp's loads are coalesced; a thread issues the loads of
+// four limbs before it recodes any, so their latencies overlap.
+template <bool XC, int KB = 128>
 __device__ __forceinline__ void fill_x(uint8_t *xs, const uint64_t *x, int nx, int ptot) {
-  constexpr int U = 4;
-  const int total = 16 * ptot, step = (int)blockDim.x;
+  constexpr int U = 4, R = KB / 8, LR = KB == 128 ? 4 : (KB == 64 ? 3 : 2);
+  const int total = R * ptot, step = (int)blockDim.x;
   for (int i0 = threadIdx.x; i0 < total; i0 += U * step) {
     uint64_t v[U], below[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const int L = i0 + u * step - 256;
-      v[u] = (L >= 0 && L < nx && L + 256 < total) ? x[L] : 0ull;
-      below[u] = (L >= 1 && L - 1 < nx && (XC || L < nx) && L + 256 < total) ? x[L - 1] : 0ull;
+      const int i = i0 + u * step, L = i - 16 * R;
+      v[u] = (L >= 0 && L < nx && i < total) ? x[L] : 0ull;
+      below[u] = (L >= 1 && L - 1 < nx && (XC || L < nx) && i < total) ? x[L - 1] : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int i = i0 + u * step;
       if (i < total) {
-        const int pp = i >> 4, h = i & 15;
+        const int pp = i >> LR, h = i & (R - 1);
         const Digits16 d = recode16(v[u], below[u]);
         const uint32_t el = (uint32_t)d.ev, eh = (uint32_t)(d.ev >> 32);
         const uint32_t ol = (uint32_t)d.od, oh = (uint32_t)(d.od >> 32);
@@ -347,9 +369,9 @@ struct HankLimbs {
   uint64_t hi, lo;
 };
 
-template <int G>
+template <int G, int KB = 128>
 __device__ __forceinline__ HankLimbs hank_load(const uint64_t *y, int ny, int eb, int t) {
-  constexpr int HB = hankel_blocks(G);
+  constexpr int HB = hankel_blocks(G, KB);
   HankLimbs v{0ull, 0ull};
   if (t <= HB) {
     const int64_t U = 16ll * eb + 15 - t;
@@ -359,15 +381,16 @@ __device__ __forceinline__ HankLimbs hank_load(const uint64_t *y, int ny, int eb
   return v;
 }
 
-template <int G>
-__host__ __device__ constexpr int hank_stage_words() { return 4 * hankel_blocks(G) + 20; }
+template <int G, int KB = 128>
+__host__ __device__ constexpr int hank_stage_words() { return 4 * hankel_blocks(G, KB) + 20; }
 
-template <int G, int NTH>
+template <int G, int NTH, int KB = 128>
 __device__ __forceinline__ void hank_build(uint8_t *hb, uint8_t *st, HankLimbs v, int t) {
-  constexpr int HB = hankel_blocks(G);
+  constexpr int HB = hankel_blocks(G, KB);
   static_assert(HB + 1 <= NTH && NTH % 32 == 0, "one limb per staging thread");
-  static_assert(2 * hank_stage_words<G>() * 4 <= 32 * 128 * 4, "staging fits the column-sum area");
-  uint32_t *D0 = reinterpret_cast<uint32_t *>(st), *D1 = D0 + hank_stage_words<G>();
+  static_assert(2 * hank_stage_words<G, KB>() * 4 <= 32 * 128 * 4,
+                "staging fits the 32 columns of the column-sum area");
+  uint32_t *D0 = reinterpret_cast<uint32_t *>(st), *D1 = D0 + hank_stage_words<G, KB>();
   if (t <= HB) {
     // D[8 t + w] = digit 7 - w of limb U; the second copy starts at D[1]
     const Digits16 d = recode16(v.hi, v.lo);
@@ -388,34 +411,39 @@ __device__ __forceinline__ void hank_build(uint8_t *hb, uint8_t *st, HankLimbs v
 }
 
 // Thread 0: the MMAs of one group (blocks ea..eb) into the accumulator at
-// TMEM column dtm, then a commit to mbar.  For block e only the columns of
-// the tile that meet x (c - e in [0, mx)) are computed, widened to multiples
-// of 16; the group's first MMA overwrites the accumulator if it spans the
-// group's columns (group_span), otherwise a clearing MMA with a zero A
-// operand over those columns comes first.
+// TMEM column dtm, then a commit to mbar.  Block e (y digits around 128 e)
+// meets x block p in output column p + S e (S = 128 / KB); only the columns
+// of the tile that meet x are computed, widened to multiples of 16; the
+// group's first MMA overwrites the accumulator if it spans the group's
+// columns (group_span), otherwise a clearing MMA with a zero A operand over
+// those columns comes first.
 // Tile columns [lo, hi) (multiples of 16) that the MMAs of blocks ea..eb
-// write: block e meets columns [max(c0, e), min(c0 + W, e + mx)), both ends
-// growing with e.
+// write: block e meets columns [max(c0, S e), min(c0 + W, S e + mx)), both
+// ends growing with e.
+template <int KB = 128>
 __device__ __forceinline__ void group_span(int c0, int W, int ea, int eb, int mx, int &lo,
                                            int &hi) {
-  lo = ((c0 > ea ? c0 : ea) - c0) & ~15;
-  hi = ((c0 + W < eb + mx ? c0 + W : eb + mx) - c0 + 15) & ~15;
+  constexpr int S = 128 / KB;
+  lo = ((c0 > S * ea ? c0 : S * ea) - c0) & ~15;
+  hi = ((c0 + W < S * eb + mx ? c0 + W : S * eb + mx) - c0 + 15) & ~15;
 }
 
+template <int KB = 128>
 __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t xs_a,
                                             uint32_t z_a, uint32_t lbo_b, int c0, int W, int ea,
                                             int eb, int mx, uint32_t mbar) {
+  constexpr int S = 128 / KB;
   tc_fence_after();
   int slo, shi;
-  group_span(c0, W, ea, eb, mx, slo, shi);
+  group_span<KB>(c0, W, ea, eb, mx, slo, shi);
   bool first = true;
   for (int e = ea; e <= eb; e++) {
-    const int ca = (c0 > e ? c0 : e) - c0;
-    const int cb = (c0 + W < e + mx ? c0 + W : e + mx) - c0;
+    const int ca = (c0 > S * e ? c0 : S * e) - c0;
+    const int cb = (c0 + W < S * e + mx ? c0 + W : S * e + mx) - c0;
     const int lo = ca & ~15, hi = (cb + 15) & ~15;
     const uint32_t id = IDESC_M128 | ((uint32_t)((hi - lo) >> 3) << 17);
     const uint32_t aa = ha + (uint32_t)(16 * (eb - e)) * 128u;
-    const uint32_t ba = xs_a + (uint32_t)(c0 + lo - e + 16) * 16u;
+    const uint32_t ba = xs_a + (uint32_t)(c0 + lo - S * e + 16) * 16u;
     uint32_t accf = 1;
     if (first) {  // columns outside the span are neither written nor drained
       first = false;
@@ -431,7 +459,7 @@ __device__ __forceinline__ void issue_group(uint32_t dtm, uint32_t ha, uint32_t 
     uint64_t da = sdesc(aa, 128, 128), db = sdesc(ba, lbo_b, 128);
     const uint64_t step_b = (2u * lbo_b) >> 4;
 #pragma unroll
-    for (int s = 0; s < 8; s++) {
+    for (int s = 0; s < KB / 16; s++) {
       mma_f16(dtm + (uint32_t)lo, da, db, id, s == 0 ? accf : 1u);
       da += 16;
       db += step_b;
@@ -553,17 +581,32 @@ __device__ void tc_release(TcCtx &c) {
 // tiles of one product can so run on different CTAs; tc_split_finish then
 // links them (Sec. VI's per-instance work spread over several SMs).
 //
+// Narrow x blocks (KB = 64 or 32 digits, S = 128 / KB): an MMA then covers
+// S times as many output columns for the same 4 KB A operand, which is what
+// bounds narrow MMAs.  Column c holds, in its 128 rows, partial sums of the
+// coefficients KB c .. KB c + 127, so coefficient KB c + u (u < KB) is the
+// sum over a < S of row u + KB a of column c - a (each pair of digits is
+// counted in exactly one of them: x digit KB p + k and y digit d meet in
+// block e = floor((d + k) / 128) only).  The column-sum pass adds the S
+// rows; the S - 1 columns before each run of 32 are kept in shared memory,
+// and band mode starts the tiles S - 1 columns early, so that the first
+// limb kept has all of its parts.  G KB <= 1024 keeps each accumulator's
+// partial sums within 2^24 as for KB = 128.  Not with SPLIT.
+//
 // Returns false (and sets c.aborted) if a wait hit its limit.
-template <int NT, int G, bool IW = false, bool XC = true, bool SPLIT = false>
+template <int NT, int G, bool IW = false, bool XC = true, bool SPLIT = false, int KB = 128>
 __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, const uint64_t *y,
                                            int ny, uint64_t *out, int nout, int lo, int tile = 0,
                                            uint64_t *tile_carry = nullptr) {
   constexpr int DRAIN = 2 * NT;                // threads that drain and build
   constexpr int THREADS = DRAIN + (IW ? 32 : 0);
+  constexpr int S = 128 / KB, R = KB / 8;      // rows per coefficient, limbs per column
+  static_assert(G * KB <= 1024, "partial sums of a group stay within 2^24");
+  static_assert(KB == 128 || !SPLIT, "split tiles with 128-digit columns only");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = IW ? tid == DRAIN : tid == 0;
   const bool worker = !IW || tid < DRAIN;
-  const Layout Ly = layout<NT, G, XC>(nx, ny);
+  const Layout Ly = layout<NT, G, XC, KB>(nx, ny);
   uint8_t *sm = c.sm;
   const uint32_t sbase = c.sbase;
   const uint32_t xs_a = sbase + Ly.xs, z_a = sbase + Ly.z;
@@ -577,37 +620,42 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
 
   for (int i = tid; i < ZB * 128 / 16; i += THREADS)
     reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
-  fill_x<XC>(sm + Ly.xs, x, nx, Ly.ptot);
+  if (S > 1)  // no columns before the first one
+    for (int i = tid; i < (S - 1) * 128; i += THREADS) Cs[32 * 128 + i] = 0u;
+  fill_x<XC, KB>(sm + Ly.xs, x, nx, Ly.ptot);
   if (tid == 0) { c.sh->carry_hi = 0; c.sh->carry = 0; c.sh->borrow = 0; }
   fence_async_smem();
   __syncthreads();
 
-  int L0 = -1;  // first limb of the first computed tile
+  int L0 = -1;  // first limb kept (that of the first computed tile, or limb lo's column)
   // band mode: tiles anchored at the column of limb lo rather than at 0, so
   // that the columns below it (a whole tile of them, or most of one) are
-  // not computed
-  const int cfirst = lo > 0 ? lo / 16 : 0;
-  for (int c0 = cfirst; 16 * c0 < nout; c0 += NT) {
+  // not computed (with narrow blocks from S - 1 columns before it, whose
+  // rows hold parts of its coefficients)
+  const int cfirst = lo > 0 ? (lo / R - (S - 1) > 0 ? lo / R - (S - 1) : 0) : 0;
+  for (int c0 = cfirst; R * c0 < nout; c0 += NT) {
     int W = Ly.ctot - c0;
     if (W > NT) W = NT;
-    const int need = (nout - 16 * c0 + 15) / 16;  // columns holding limbs < nout
+    const int need = (nout - R * c0 + R - 1) / R;  // columns holding limbs < nout
     if (W > need) W = need;
     W = (W + 15) & ~15;
-    if (16 * (c0 + W) <= lo) continue;  // band: the whole tile lies below limb lo
+    if (R * (c0 + W) <= lo) continue;  // band: the whole tile lies below limb lo
     if (SPLIT && c0 != NT * tile) continue;
     if (L0 < 0) {
-      L0 = 16 * c0;
+      L0 = lo > 0 ? R * (lo / R) : R * c0;
       if (lo > 0 && tid == 0) c.sh->carry_hi = 1ull << 32;  // + 2^32 B^L0
     }
-    const int e_lo = c0 - Ly.mx + 1 > 0 ? c0 - Ly.mx + 1 : 0;
-    const int e_hi = c0 + W - 1 < Ly.ey ? c0 + W - 1 : Ly.ey;
+    // blocks e whose columns [S e, S e + mx) meet the tile's [c0, c0 + W)
+    const int e_lo = c0 - Ly.mx + 1 > 0 ? (c0 - Ly.mx + S) / S : 0;
+    const int e_hi = (c0 + W - 1) / S < Ly.ey ? (c0 + W - 1) / S : Ly.ey;
     const int NG = e_hi >= e_lo ? (e_hi - e_lo + G) / G : 0;
 #pragma unroll
     for (int i = 0; i < 64; i++) acc[i] = 0;
     if (NG > 0) {
       if (worker)
-        hank_build<G, DRAIN>(sm + Ly.h0, sm + Ly.cs,
-                             hank_load<G>(y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid), tid);
+        hank_build<G, DRAIN, KB>(
+            sm + Ly.h0, sm + Ly.cs,
+            hank_load<G, KB>(y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid), tid);
       fence_async_smem();
       __syncthreads();
       bool bad = false;
@@ -615,15 +663,15 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
         const int b = gi & 1;
         const int ea = e_lo + gi * G, eb = ea + G - 1 < e_hi ? ea + G - 1 : e_hi;
         if (issuer)
-          issue_group(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a, z_a,
-                      lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
+          issue_group<KB>(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a,
+                          z_a, lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
         c.pending |= 1u << b;
         // the next group's y limbs are fetched before the wait
         const bool more = gi + 1 < NG && worker;
         HankLimbs hv{0ull, 0ull};
         if (more) {
           const int na = ea + G;
-          hv = hank_load<G>(y, ny, na + G - 1 < e_hi ? na + G - 1 : e_hi, tid);
+          hv = hank_load<G, KB>(y, ny, na + G - 1 < e_hi ? na + G - 1 : e_hi, tid);
         }
         if (gi >= 1) {  // group gi-1 used the other buffers
           const int ob = b ^ 1;
@@ -635,10 +683,10 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           }
           tc_fence_after();
           int slo, shi;
-          group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
+          group_span<KB>(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
           if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
         }
-        if (more) hank_build<G, DRAIN>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
+        if (more) hank_build<G, DRAIN, KB>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
         tc_fence_before();
         fence_async_smem();
         if (__syncthreads_or(bad)) { c.aborted = true; return false; }
@@ -653,7 +701,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
       tc_fence_after();
       {
         int slo, shi;
-        group_span(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
+        group_span<KB>(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
         if (worker) drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
       }
       tc_fence_before();
@@ -661,8 +709,11 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
     }
 
     // ---- column sums -> limbs of this tile (low words to out, high words to His)
-    const int j0 = 16 * c0;
-    const int nl = 16 * W < nout - j0 ? 16 * W : nout - j0;
+    // Cs: columns 0..31 of the current run of 32, then at 32 .. 32 + S - 2
+    // the S - 1 columns before it (virtual columns -(S - 1) .. -1)
+    const int j0 = R * c0;
+    const int nl = R * W < nout - j0 ? R * W : nout - j0;
+    const int skip = L0 > j0 ? L0 - j0 : 0;  // band: limbs below L0 are not kept
 #pragma unroll
     for (int rr = 0; rr < NT / 32; rr++) {
       if (32 * rr < W) {
@@ -672,13 +723,21 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           for (int i = 0; i < 32; i++) Cs[i * 128 + t] = (uint32_t)acc[(rr & 1) * 32 + i];
         }
         __syncthreads();
-        for (int idx = tid; idx < 32 * 16; idx += THREADS) {  // 32 columns x 16 limbs
-          const int col = idx >> 4, jj = idx & 15;
-          const int lt = (32 * rr + col) * 16 + jj;
-          if (lt < nl) {
-            const uint4 u0 = *reinterpret_cast<const uint4 *>(&Cs[col * 128 + 8 * jj]);
-            const uint4 u1 = *reinterpret_cast<const uint4 *>(&Cs[col * 128 + 8 * jj + 4]);
-            const uint32_t cw[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        for (int idx = tid; idx < 32 * R; idx += THREADS) {  // 32 columns x R limbs
+          const int col = idx / R, jj = idx % R;
+          const int lt = (32 * rr + col) * R + jj;
+          if (lt < nl && lt >= skip) {
+            uint32_t cw[8];
+#pragma unroll
+            for (int a = 0; a < S; a++) {  // row 8 jj + KB a of column col - a
+              const int v = col - a, slot = v >= 0 ? v : 32 + S - 1 + v;
+              const uint4 u0 = *reinterpret_cast<const uint4 *>(&Cs[slot * 128 + 8 * jj + KB * a]);
+              const uint4 u1 =
+                  *reinterpret_cast<const uint4 *>(&Cs[slot * 128 + 8 * jj + KB * a + 4]);
+              const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+              for (int k = 0; k < 8; k++) cw[k] = a == 0 ? w[k] : cw[k] + w[k];
+            }
             unsigned __int128 V = 0;
 #pragma unroll
             for (int k = 0; k < 8; k++) V += (unsigned __int128)(cw[k] ^ 0x80000000u) << (8 * k);
@@ -687,14 +746,21 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           }
         }
         __syncthreads();
+        if (S > 1) {  // the last S - 1 columns of this run precede the next one
+          for (int i = tid; i < (S - 1) * 128; i += THREADS)
+            Cs[32 * 128 + i] = Cs[(33 - S) * 128 + i];
+          __syncthreads();
+        }
       }
     }
     {
+      // band mode's first tile: the kept limbs start at L0 (skip > 0), with
+      // the margin (carry_hi = 2^32) in place of what limb L0 - 1 would carry
       const uint64_t hprev = c.sh->carry_hi;
       const uint32_t cprev = c.sh->carry;
-      uint64_t *o = out + j0;
+      uint64_t *o = out + j0 + skip;
       auto load = [&](int j) {
-        return make_ulonglong2(o[j], j == 0 ? hprev : (uint64_t)His[j - 1]);
+        return make_ulonglong2(o[j], j == 0 ? hprev : (uint64_t)His[skip + j - 1]);
       };
       auto store = [&](int j, uint64_t v) { o[j] = v; };
       if (SPLIT) {
@@ -710,9 +776,9 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
         // into the next tile
         uint32_t cc = cprev, bb = c.sh->borrow;
         auto bias = [&](int j) {
-          return j0 + j == L0 ? 0x8080808080000000ull : 0x8080808080808080ull;
+          return j0 + skip + j == L0 ? 0x8080808080000000ull : 0x8080808080808080ull;
         };
-        blk_add_then_sub(nl, &cc, &bb, load, bias, store, c.scr);
+        blk_add_then_sub(nl - skip, &cc, &bb, load, bias, store, c.scr);
         if (tid == 0) {
           c.sh->carry_hi = His[nl - 1];
           c.sh->carry = cc;

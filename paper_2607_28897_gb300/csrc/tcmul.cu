@@ -9,23 +9,13 @@
 namespace bigint {
 namespace tcm {
 
-// Asks L2 for the 16-byte-aligned part of [p, p + bytes) (no completion to
-// wait for): the next instance's operands come in from HBM while this one
-// is computed, so its first loads meet L2 rather than HBM.
-__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
-  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
-  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
-  if (e > a)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a))
-                 : "memory");
-}
-
-// 2 NT drain threads plus one issuer warp (tc_product<NT, G, true, XC>).
+// 2 NT drain threads plus one issuer warp (tc_product<NT, G, true, XC, false,
+// KB>).
 // Instance i's operands start at X + i sx and Y + i sy, its result at
 // Out + i so (limbs); lo > 0 is tc_product's band mode.  A CTA that gives up
 // at a wait limit also sets *abort_flag (if given), so that a caller
 // chaining products (the step-batched division) can report it per instance.
-template <int NT, int G, bool XC>
+template <int NT, int G, bool XC, int KB = 128>
 __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
     k_mul_tc(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
              uint64_t *__restrict__ Out, int nx, int ny, int nout, int64_t count, int64_t sx,
@@ -41,8 +31,8 @@ __global__ void __launch_bounds__(2 * NT + 32, 256 / NT)
       prefetch_l2(X + next * sx, 8 * (size_t)nx);
       prefetch_l2(Y + next * sy, 8 * (size_t)ny);
     }
-    if (!tc_product<NT, G, true, XC>(c, X + inst * sx, nx, Y + inst * sy, ny, Out + inst * so,
-                                     nout, lo))
+    if (!tc_product<NT, G, true, XC, false, KB>(c, X + inst * sx, nx, Y + inst * sy, ny,
+                                                Out + inst * so, nout, lo))
       break;
   }
   if (c.aborted && abort_flag != nullptr && threadIdx.x == 0) atomicExch(abort_flag, 1);
@@ -149,7 +139,7 @@ __global__ void __launch_bounds__(512)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <int NT, int G, bool XC>
+template <int NT, int G, bool XC, int KB>
 static int tc_dyn_max() {
   static int dyn = -1;
   if (dyn < 0) {
@@ -159,9 +149,9 @@ static int tc_dyn_max() {
         cudaSuccess)
       return 0;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC, KB>) != cudaSuccess) return 0;
     const int d = optin - (int)fa.sharedSizeBytes;
-    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT, G, XC>,
+    if (cudaFuncSetAttribute(tcm::k_mul_tc<NT, G, XC, KB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, d) != cudaSuccess)
       return 0;
     dyn = d;
@@ -169,69 +159,62 @@ static int tc_dyn_max() {
   return dyn;
 }
 
-// The kernel shape of an nx x ny product (nx <= ny).  Output columns of 128
-// digits: ctot = mx + ey.  A product whose columns fit 128 runs the 128-column
-// tile, two CTAs per SM; one that fits only without x's carry digit (square
-// products of 1024 limbs: 129 -> 128 columns) drops it (XC = false: one
-// correction addition); larger ones run the 256-column tile, one CTA per SM.
-// Products whose columns fit 64 (square products up to 512 limbs, without
-// the carry digit where needed) run a 64-column tile with groups of 7 blocks,
-// three CTAs per SM: at such sizes an MMA's time is set by reading its
-// 4 KB A operand from shared memory rather than by N, and one issuing CTA
-// reaches about two thirds of that rate, so three CTAs keep the tensor core
-// busy while the others drain, build and finish their products.
-// (Dropping the carry digit where the tile does not change costs 1-4 %.)
-enum TcShape { TC_64_XC, TC_64_NOXC, TC_128_XC, TC_128_NOXC, TC_256 };
+// The kernel shapes (tile columns NT, group G, x's carry digit XC, x block
+// width KB).  128-digit blocks: the 256-column tile, one CTA per SM, for
+// large products; the 128- and 64-column tiles (two and three CTAs per SM)
+// for products whose columns fit one such tile, x's carry digit dropped
+// (XC = false: one correction addition) where that makes them fit.  Narrow
+// blocks (64 or 32 digits, 128-column tiles, two CTAs per SM) give each MMA
+// 2 or 4 times the columns for the same 4 KB A operand, which bounds narrow
+// MMAs; measured on GB300 they tie with 128-digit blocks at 512-limb
+// products and lose from 1024 limbs on (4x the drains and column-sum rows
+// per digit), so only the autotuner and the forced variants take them.
+enum TcShape {
+  TC_64_XC, TC_64_NOXC, TC_128_XC, TC_128_NOXC, TC_256,
+  TC_N64_XC, TC_N64_NOXC, TC_N32_XC, TC_N32_NOXC, TC_NSHAPES
+};
+struct ShapeInfo {
+  int nt, g, kb;
+  bool xc;
+};
+static constexpr ShapeInfo SHAPES[TC_NSHAPES] = {
+    {64, 7, 128, true},   {64, 7, 128, false},  {128, 8, 128, true}, {128, 8, 128, false},
+    {256, 8, 128, true},  {128, 15, 64, true},  {128, 15, 64, false}, {128, 12, 32, true},
+    {128, 12, 32, false}};
 
-static TcShape tc_shape(int nx, int ny) {
-  const int ey = (8 * ny + 127) / 128;
-  const int cx = (8 * nx + 1 + 127) / 128 + ey, c0 = (8 * nx + 127) / 128 + ey;
-  if (cx <= 64) return TC_64_XC;
-  if (c0 <= 64) return TC_64_NOXC;
-  if (cx <= 128) return TC_128_XC;
-  if (c0 <= 128) return TC_128_NOXC;
-  return TC_256;
-}
-
-// The same choice for the columns a product actually computes: the low nout
-// limbs (nout < nx + ny) and, in band mode, only the columns from the one
-// that holds limb lo (tc_product's tiles start there).  A low or banded
-// product often needs far fewer columns than the full one, and the smaller
-// tile then runs several CTAs per SM.
-static TcShape tc_shape_cols(int nx, int ny, int nout, int lo) {
-  const int ey = (8 * ny + 127) / 128;
-  const int need = (nout + 15) / 16, first = lo > 0 ? lo / 16 : 0;
-  auto width = [&](int mx) { return (mx + ey < need ? mx + ey : need) - first; };
-  const int wx = width((8 * nx + 1 + 127) / 128), w0 = width((8 * nx + 127) / 128);
-  if (wx <= 64) return TC_64_XC;
-  if (w0 <= 64) return TC_64_NOXC;
-  if (wx <= 128) return TC_128_XC;
-  if (w0 <= 128) return TC_128_NOXC;
-  return TC_256;
-}
-
-template <int NT, int G, bool XC>
+template <int NT, int G, bool XC, int KB>
 static size_t tc_smem(int nx, int ny) {
-  const tcm::Layout L = tcm::layout<NT, G, XC>(nx, ny);
-  const int d = tc_dyn_max<NT, G, XC>();
+  const tcm::Layout L = tcm::layout<NT, G, XC, KB>(nx, ny);
+  const int d = tc_dyn_max<NT, G, XC, KB>();
   return d > 0 && L.total <= (uint32_t)d ? L.total : 0;
 }
 
+// Shared memory of a shape for x of nx and y of ny limbs, 0 if it does not
+// fit (the 256-column tile falls back to groups of 4 blocks).
+static size_t shape_smem(TcShape sh, int nx, int ny) {
+  switch (sh) {
+    case TC_64_XC: return tc_smem<64, 7, true, 128>(nx, ny);
+    case TC_64_NOXC: return tc_smem<64, 7, false, 128>(nx, ny);
+    case TC_128_XC: return tc_smem<128, 8, true, 128>(nx, ny);
+    case TC_128_NOXC: return tc_smem<128, 8, false, 128>(nx, ny);
+    case TC_N64_XC: return tc_smem<128, 15, true, 64>(nx, ny);
+    case TC_N64_NOXC: return tc_smem<128, 15, false, 64>(nx, ny);
+    case TC_N32_XC: return tc_smem<128, 12, true, 32>(nx, ny);
+    case TC_N32_NOXC: return tc_smem<128, 12, false, 32>(nx, ny);
+    default: {
+      const size_t s8 = tc_smem<256, 8, true, 128>(nx, ny);
+      return s8 ? s8 : tc_smem<256, 4, true, 128>(nx, ny);
+    }
+  }
+}
+
 // Dynamic shared memory the tensor-core product of an na x nb product
-// needs, or 0 if it does not fit (or the shapes are out of range).
+// needs with the 256-column tile (which every product that fits any shape
+// fits), or 0 if it does not fit (or the shapes are out of range).
 size_t mul_tc_smem(int na, int nb) {
   const int nx = na < nb ? na : nb, ny = na < nb ? nb : na;
   if (nx < 1 || nx > 16383 || ny > 32768) return 0;
-  switch (tc_shape(nx, ny)) {
-    case TC_64_XC: return tc_smem<64, 7, true>(nx, ny);
-    case TC_64_NOXC: return tc_smem<64, 7, false>(nx, ny);
-    case TC_128_XC: return tc_smem<128, 8, true>(nx, ny);
-    case TC_128_NOXC: return tc_smem<128, 8, false>(nx, ny);
-    default: {
-      const size_t s8 = tc_smem<256, 8, true>(nx, ny);
-      return s8 ? s8 : tc_smem<256, 4, true>(nx, ny);
-    }
-  }
+  return shape_smem(TC_256, nx, ny);
 }
 
 // Operands and results of one batched product launch: instance i's x at
@@ -245,73 +228,169 @@ struct TcArgs {
   int *abort_flag;
 };
 
-template <int NT, int G, bool XC>
-static int launch_tc(const TcArgs &A, int64_t count, int nx, int ny, int nout, cudaStream_t st) {
-  const size_t smem = tc_smem<NT, G, XC>(nx, ny);
-  if (smem == 0) return BIGINT_EINVAL;
-  if (count == 0) return BIGINT_OK;
-  // device and kernel attributes, read once (a division issues dozens of
-  // these launches back to back)
-  static int sms = 0, smem_sm = 0, reserved = 0, static_smem = 0;
-  if (sms == 0) {
-    int dev = 0, n = 0;
-    BIGINT_CUDA_TRY(cudaGetDevice(&dev));
-    BIGINT_CUDA_TRY(
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    BIGINT_CUDA_TRY(
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+// CTAs of a shape resident on one SM: TMEM allows 256 / NT, shared memory
+// per SM / (dynamic + static + the per-block reservation).
+template <int NT, int G, bool XC, int KB>
+static int tc_per_sm(size_t smem) {
+  static int smem_sm = 0, reserved = 0, static_smem = -1;
+  if (static_smem < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess)
+      return 1;
     cudaFuncAttributes fa;
-    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC>));
+    if (cudaFuncGetAttributes(&fa, tcm::k_mul_tc<NT, G, XC, KB>) != cudaSuccess) return 1;
     static_smem = (int)fa.sharedSizeBytes;
-    BIGINT_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-    sms = n;
   }
-  // CTAs resident at once on an SM: TMEM allows 256 / NT, shared memory
-  // per SM / (dynamic + static + the per-block reservation)
   int per_sm = smem_sm / (int)(smem + static_smem + reserved);
   if (per_sm > 256 / NT) per_sm = 256 / NT;
-  if (per_sm < 1) per_sm = 1;
-  const int64_t slots = (int64_t)sms * per_sm;
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  }
+  return sms;
+}
+
+template <int NT, int G, bool XC, int KB>
+static int launch_tc(const TcArgs &A, int64_t count, int nx, int ny, int nout, cudaStream_t st) {
+  const size_t smem = tc_smem<NT, G, XC, KB>(nx, ny);
+  if (smem == 0) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  const int sms = sm_count();
+  if (sms == 0) return BIGINT_ECUDA;
+  const int64_t slots = (int64_t)sms * tc_per_sm<NT, G, XC, KB>(smem);
   const int64_t grid = count < slots ? count : slots;
-  tcm::k_mul_tc<NT, G, XC><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(
+  tcm::k_mul_tc<NT, G, XC, KB><<<(unsigned)grid, 2 * NT + 32, smem, st>>>(
       A.x, A.y, A.out, nx, ny, nout, count, A.sx, A.sy, A.so, A.lo, A.abort_flag);
   return bigint_launch_status();
 }
 
-// Products with strides and a band start (see TcArgs); the shorter operand
-// becomes x.  The column sums stay below 2^31 while the shorter operand has
-// at most 16383 limbs (a column has at most 8 nx + 1 digit products); the
-// longer one only sets how many Toeplitz blocks there are.
-// Toeplitz blocks (each eight MMAs) the tiles of a product with x of nx and
-// y of ny limbs issue, following tc_product's tile loop: for each tile the
-// blocks e whose columns meet x.
-static long tc_blocks(int nx, int ny, int nout, int lo, int NT, bool XC) {
-  const int mx = (8 * nx + (XC ? 1 : 0) + 127) / 128, ey = (8 * ny + 127) / 128;
-  const int ctot = mx + ey, cfirst = lo > 0 ? lo / 16 : 0;
-  long blocks = 0;
-  for (int c0 = cfirst; 16 * c0 < nout; c0 += NT) {
-    int W = ctot - c0;
-    if (W > NT) W = NT;
-    const int need = (nout - 16 * c0 + 15) / 16;
-    if (W > need) W = need;
-    W = (W + 15) & ~15;
-    if (16 * (c0 + W) <= lo) continue;
-    const int e_lo = c0 - mx + 1 > 0 ? c0 - mx + 1 : 0;
-    const int e_hi = c0 + W - 1 < ey ? c0 + W - 1 : ey;
-    if (e_hi >= e_lo) blocks += e_hi - e_lo + 1;
+static int launch_shape(TcShape sh, const TcArgs &A, int64_t count, int nx, int ny, int nout,
+                        cudaStream_t st) {
+  switch (sh) {
+    case TC_64_XC: return launch_tc<64, 7, true, 128>(A, count, nx, ny, nout, st);
+    case TC_64_NOXC: return launch_tc<64, 7, false, 128>(A, count, nx, ny, nout, st);
+    case TC_128_XC: return launch_tc<128, 8, true, 128>(A, count, nx, ny, nout, st);
+    case TC_128_NOXC: return launch_tc<128, 8, false, 128>(A, count, nx, ny, nout, st);
+    case TC_N64_XC: return launch_tc<128, 15, true, 64>(A, count, nx, ny, nout, st);
+    case TC_N64_NOXC: return launch_tc<128, 15, false, 64>(A, count, nx, ny, nout, st);
+    case TC_N32_XC: return launch_tc<128, 12, true, 32>(A, count, nx, ny, nout, st);
+    case TC_N32_NOXC: return launch_tc<128, 12, false, 32>(A, count, nx, ny, nout, st);
+    default:
+      return tc_smem<256, 8, true, 128>(nx, ny)
+                 ? launch_tc<256, 8, true, 128>(A, count, nx, ny, nout, st)
+                 : launch_tc<256, 4, true, 128>(A, count, nx, ny, nout, st);
   }
-  return blocks;
 }
 
-static int tc_nt(TcShape sh) { return sh == TC_256 ? 256 : (sh >= TC_128_XC ? 128 : 64); }
-static bool tc_xc(TcShape sh) { return sh == TC_64_XC || sh == TC_128_XC || sh == TC_256; }
+// Modelled tensor-core cycles of one product of a shape (x of nx, y of ny
+// limbs, low nout limbs, band start lo), following tc_product's tile loop:
+// each MMA of N columns costs the larger of its math (128 x N x 16 fp16
+// multiply-adds at ~6750 flop/cycle per SM) and its operand reads from
+// shared memory (4 KB of A plus 32 N bytes of B at 128 bytes/cycle); the
+// tiles (each a fixed cost: its first Hankel build, last drain and column
+// sums) count 4000 cycles.  tiles_out: the product's tiles.
+static double tc_model(TcShape sh, int nx, int ny, int nout, int lo, int *tiles_out = nullptr) {
+  const ShapeInfo &I = SHAPES[sh];
+  const int KB = I.kb, S = 128 / KB, R = KB / 8, NT = I.nt;
+  const int mx = (8 * nx + (I.xc ? 1 : 0) + KB - 1) / KB, ey = (8 * ny + KB - 1) / 128;
+  const int ctot = mx + S * ey + S - 1;
+  const int cfirst = lo > 0 ? (lo / R - (S - 1) > 0 ? lo / R - (S - 1) : 0) : 0;
+  double cyc = 0;
+  int tiles = 0;
+  for (int c0 = cfirst; R * c0 < nout; c0 += NT) {
+    int W = ctot - c0;
+    if (W > NT) W = NT;
+    const int need = (nout - R * c0 + R - 1) / R;
+    if (W > need) W = need;
+    W = (W + 15) & ~15;
+    if (R * (c0 + W) <= lo) continue;
+    tiles++;
+    const int e_lo = c0 - mx + 1 > 0 ? (c0 - mx + S) / S : 0;
+    const int e_hi = (c0 + W - 1) / S < ey ? (c0 + W - 1) / S : ey;
+    for (int e = e_lo; e <= e_hi; e++) {
+      const int ca = (c0 > S * e ? c0 : S * e) - c0, cb = (c0 + W < S * e + mx ? c0 + W : S * e + mx) - c0;
+      const int N = ((cb + 15) & ~15) - (ca & ~15);
+      const double math = 4096.0 * N / 6750.0, rd = 32.0 + N / 4.0;
+      cyc += (KB / 16) * (math > rd ? math : rd);
+    }
+  }
+  if (tiles_out) *tiles_out = tiles;
+  return cyc + 4000.0 * tiles;
+}
 
-// force_nt: 0 (the tile by the columns computed, as below) or the tile's
-// column count 64, 128 or 256 (the autotuner's candidates); a forced 64- or
-// 128-column tile drops x's carry digit where that saves a tile.
+// Whether a shape computes the product at all: the 64- and 128-column tiles
+// of 128-digit blocks take products whose columns fit one tile; the others
+// any number of tiles.
+static bool shape_applies(TcShape sh, int nx, int ny, int nout, int lo) {
+  const ShapeInfo &I = SHAPES[sh];
+  if (I.kb != 128 || I.nt == 256) return true;
+  int tiles = 0;
+  tc_model(sh, nx, ny, nout, lo, &tiles);
+  return tiles <= 1;
+}
+
+// Modelled time of a product on one SM: tensor-core cycles, shared by the
+// CTAs resident on it; with one CTA per SM the setup, first Hankel build,
+// last drains and column sums of each product do not overlap another CTA's
+// MMAs, which the model charges as 15 % more.
+static double shape_cost(TcShape sh, int nx, int ny, int nout, int lo) {
+  if (!shape_applies(sh, nx, ny, nout, lo)) return -1;
+  const size_t smem = shape_smem(sh, nx, ny);
+  if (smem == 0) return -1;
+  int per_sm = 1;
+  switch (sh) {
+    case TC_64_XC: per_sm = tc_per_sm<64, 7, true, 128>(smem); break;
+    case TC_64_NOXC: per_sm = tc_per_sm<64, 7, false, 128>(smem); break;
+    case TC_128_XC: per_sm = tc_per_sm<128, 8, true, 128>(smem); break;
+    case TC_128_NOXC: per_sm = tc_per_sm<128, 8, false, 128>(smem); break;
+    case TC_N64_XC: per_sm = tc_per_sm<128, 15, true, 64>(smem); break;
+    case TC_N64_NOXC: per_sm = tc_per_sm<128, 15, false, 64>(smem); break;
+    case TC_N32_XC: per_sm = tc_per_sm<128, 12, true, 32>(smem); break;
+    case TC_N32_NOXC: per_sm = tc_per_sm<128, 12, false, 32>(smem); break;
+    default: per_sm = 1;
+  }
+  const double c = tc_model(sh, nx, ny, nout, lo);
+  return per_sm > 1 ? c : 1.15 * c;
+}
+
+// The cheapest shape by the model for x of nx, y of ny limbs (among those
+// whose x block width is in kb_mask: bit 0 128, bit 1 64, bit 2 32, and
+// whose tile is NT when nt > 0); cost_out its modelled cost.
+static TcShape best_shape(int nx, int ny, int nout, int lo, int kb_mask, int nt,
+                          double *cost_out) {
+  TcShape best = TC_256;
+  double bc = -1;
+  for (int i = 0; i < TC_NSHAPES; i++) {
+    const TcShape sh = (TcShape)i;
+    const int kbit = SHAPES[i].kb == 128 ? 1 : (SHAPES[i].kb == 64 ? 2 : 4);
+    if (!(kb_mask & kbit) || (nt > 0 && SHAPES[i].nt != nt)) continue;
+    const double c = shape_cost(sh, nx, ny, nout, lo);
+    if (c >= 0 && (bc < 0 || c < bc)) {
+      bc = c;
+      best = sh;
+    }
+  }
+  *cost_out = bc;
+  return best;
+}
+
+// force: 0 (the 128-digit-block shape by the model, below) or one of the
+// autotuner's candidates -- TC_FORCE_64 / _128 / _256 (128-digit blocks,
+// that tile) and TC_FORCE_N64 / _N32 (narrow blocks).  The shorter operand
+// becomes x.
 int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, uint64_t *out,
                      int64_t so, int64_t count, int na, int nb, int nout, int lo, int *abort_flag,
-                     cudaStream_t st, int force_nt) {
+                     cudaStream_t st, int force) {
   TcArgs A{a, b, out, sa, sb, so, lo, abort_flag};
   int nx = na, ny = nb;
   if (nb < na) {
@@ -320,48 +399,41 @@ int launch_mul_tc_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t s
   }
   if (nx < 1 || nx > 16383 || ny > 32768 || nout < 1 || nout > na + nb || lo < 0 || lo >= nout)
     return BIGINT_EINVAL;
+  if (shape_smem(TC_256, nx, ny) == 0) return BIGINT_EINVAL;
+  int kb_mask = 1, nt = 0;
+  switch (force) {
+    case 0: break;
+    case TC_FORCE_64: kb_mask = 1; nt = 64; break;
+    case TC_FORCE_128: kb_mask = 1; nt = 128; break;
+    case TC_FORCE_256: kb_mask = 1; nt = 256; break;
+    case TC_FORCE_N64: kb_mask = 2; break;
+    case TC_FORCE_N32: kb_mask = 4; break;
+    default: return BIGINT_EINVAL;
+  }
   // x is the operand stored whole in shared memory (the B side), y the one
-  // whose Toeplitz blocks are the A side.  While an MMA is narrower than
-  // ~136 columns its time is its A operand's read, so a product issues
-  // fewer MMAs, each wider, with the SHORTER operand as y when that lowers
-  // the blocks issued (a low product whose longer operand has most of the
-  // columns); the longer operand then has to fit shared memory as x.
-  TcShape sh = tc_shape_cols(nx, ny, nout, lo);
-  if (force_nt == 256) {
-    sh = TC_256;
-  } else if (force_nt == 64 || force_nt == 128) {
-    const bool drop = tc_blocks(nx, ny, nout, lo, force_nt, false) <
-                      tc_blocks(nx, ny, nout, lo, force_nt, true);
-    sh = force_nt == 64 ? (drop ? TC_64_NOXC : TC_64_XC) : (drop ? TC_128_NOXC : TC_128_XC);
-  } else if (nx != ny && ny <= 16383) {
-    const TcShape sw = tc_shape_cols(ny, nx, nout, lo);
-    const long keep = tc_blocks(nx, ny, nout, lo, tc_nt(sh), tc_xc(sh));
-    const long swap = tc_blocks(ny, nx, nout, lo, tc_nt(sw), tc_xc(sw));
-    if (tc_nt(sw) < 256 && swap < keep) {
-      size_t need = 0;
-      switch (sw) {
-        case TC_64_XC: need = tc_smem<64, 7, true>(ny, nx); break;
-        case TC_64_NOXC: need = tc_smem<64, 7, false>(ny, nx); break;
-        case TC_128_XC: need = tc_smem<128, 8, true>(ny, nx); break;
-        default: need = tc_smem<128, 8, false>(ny, nx); break;
-      }
-      if (need > 0) {
-        const uint64_t *tp = A.x; A.x = A.y; A.y = tp;
-        const int64_t ts = A.sx; A.sx = A.sy; A.sy = ts;
-        const int tn = nx; nx = ny; ny = tn;
-        sh = sw;
-      }
+  // whose Toeplitz blocks are the A side.  Either may be the shorter: the
+  // model often prefers the shorter operand as y (fewer, wider MMAs for a
+  // low product whose longer operand has most of the columns), as long as
+  // the longer one fits shared memory as x and in a column sum's range.
+  double keep = 0, swap = -1;
+  TcShape sh = best_shape(nx, ny, nout, lo, kb_mask, nt, &keep);
+  if (keep < 0 && force != 0) {  // the forced shape does not take this product
+    kb_mask = 1;
+    nt = 0;
+    sh = best_shape(nx, ny, nout, lo, kb_mask, nt, &keep);
+  }
+  if (nx != ny && ny <= 16383) {
+    const TcShape sw = best_shape(ny, nx, nout, lo, kb_mask, nt, &swap);
+    if (swap >= 0 && (keep < 0 || swap < keep)) {
+      const uint64_t *tp = A.x; A.x = A.y; A.y = tp;
+      const int64_t ts = A.sx; A.sx = A.sy; A.sy = ts;
+      const int tn = nx; nx = ny; ny = tn;
+      sh = sw;
+      keep = swap;
     }
   }
-  switch (sh) {
-    case TC_64_XC: return launch_tc<64, 7, true>(A, count, nx, ny, nout, st);
-    case TC_64_NOXC: return launch_tc<64, 7, false>(A, count, nx, ny, nout, st);
-    case TC_128_XC: return launch_tc<128, 8, true>(A, count, nx, ny, nout, st);
-    case TC_128_NOXC: return launch_tc<128, 8, false>(A, count, nx, ny, nout, st);
-    default:
-      return tc_smem<256, 8, true>(nx, ny) ? launch_tc<256, 8, true>(A, count, nx, ny, nout, st)
-                                           : launch_tc<256, 4, true>(A, count, nx, ny, nout, st);
-  }
+  if (keep < 0) return BIGINT_EINVAL;
+  return launch_shape(sh, A, count, nx, ny, nout, st);
 }
 
 int launch_mul_tc(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
@@ -566,11 +638,11 @@ int launch_split(const uint64_t *x, const uint64_t *y, uint64_t *out, int64_t co
 // and sm_103, less room for the kernel's static shared memory).
 constexpr size_t SPLIT_SMEM_CAP = 232448 - 2048;
 
-// Tiles of an nx x ny split product, or 0 if it does not run split (not on
-// the 256-column tile with the carry digit, x too large for shared memory,
+// Tiles of an nx x ny split product, or 0 if it does not run split (columns
+// of 128 digits that fit a 128-column tile, x too large for shared memory,
 // or a single tile).
 int split_tiles(int nx, int ny) {
-  if (nx < 1 || ny > 16383 || tc_shape(nx, ny) != TC_256) return 0;
+  if (nx < 1 || ny > 16383 || (8 * nx + 127) / 128 + (8 * ny + 127) / 128 <= 128) return 0;
   if (tcm::layout<SPLIT_NT, 4>(nx, ny).total > SPLIT_SMEM_CAP) return 0;
   const int T = (nx + ny + SPLIT_TILE_LIMBS - 1) / SPLIT_TILE_LIMBS;
   return T >= 2 ? T : 0;

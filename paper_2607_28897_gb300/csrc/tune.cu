@@ -68,16 +68,18 @@ std::string gpu_name() {
 }  // namespace
 
 // Candidates of the multiply tuner for an na x nb product: the tensor-core
-// product with its tile chosen by size (12) and forced to 64, 128 and 256
-// output columns (13, 14, 15) -- the tile also sets how many CTAs share an
-// SM -- and the integer products with 29-bit digits / 16-column chunks (8)
-// and 28-bit digits / 8-column chunks (9), plus one level of Karatsuba (10)
-// for square products.
+// product with its shape chosen by the cost model (12), forced to 128-digit
+// x blocks with 64, 128 and 256 output columns (13, 14, 15) -- the tile also
+// sets how many CTAs share an SM -- and to narrow x blocks of 64 and 32
+// digits (16, 17), and the integer products with 29-bit digits / 16-column
+// chunks (8) and 28-bit digits / 8-column chunks (9), plus one level of
+// Karatsuba (10) for square products.
 int tune_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na, int nb,
              cudaStream_t st, int *best_variant) {
-  int cand[8], nc = 0;
+  int cand[10], nc = 0;
   if ((na < nb ? na : nb) >= 64 && mul_tc_smem(na, nb) > 0) {
     cand[nc++] = 12; cand[nc++] = 13; cand[nc++] = 14; cand[nc++] = 15;
+    cand[nc++] = 16; cand[nc++] = 17;
   }
   cand[nc++] = 8;
   cand[nc++] = 9;

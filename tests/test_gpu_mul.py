@@ -87,7 +87,7 @@ def test_config_sweep_full_size(bi, orc, n):
     assert np.array_equal(p[idx], orc.batch_mul(a[idx], b[idx]))
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10, 12, 13, 14, 15])
+@pytest.mark.parametrize("variant", [8, 9, 10, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("n", [1, 63, 64, 65, 511, 1000, 2049])
 def test_every_variant(bi, orc, variant, n):
     """Every multiply variant (integer digit size and chunk width, Karatsuba,
