@@ -81,6 +81,9 @@ namespace tcm {
 // K of one Toeplitz block).  A group's Hankel buffer holds 16 G + KB / 8 - 1
 // core matrices.
 __host__ __device__ constexpr int hankel_blocks(int G, int KB = 128) { return 16 * G + KB / 8 - 1; }
+// 32-bit words of one copy of a group's Hankel staging run (hank_build).
+template <int G, int KB = 128>
+__host__ __device__ constexpr int hank_stage_words() { return 4 * hankel_blocks(G, KB) + 20; }
 constexpr int ZB = 18;           // zero core matrices (operand of the clearing MMA)
 // NT: output columns per tile (= MMA N at most); 2 NT threads, 2 NT TMEM
 // columns (two accumulators).
@@ -114,17 +117,22 @@ struct Layout {
   int ctot;  // output columns with nonzero coefficients: mx + S ey + S - 1 (S = 128 / KB)
   int ptot;  // stored x blocks (16 zero blocks on each side; odd)
   // byte offsets in dynamic shared memory: x (B layout), zero core matrices,
-  // the two Hankel buffers, the column-sum transpose area (also the Hankel
-  // staging run while a tile's groups run), high words of the tile's limbs
-  uint32_t xs, z, h0, h1, cs, his, total;
+  // the two Hankel buffers, the Hankel staging run, the column-sum transpose
+  // area, high words of the tile's limbs
+  uint32_t xs, z, h0, h1, st, cs, his, total;
 };
 
 // KB = 128: one output column per 128 digits, each coefficient in one TMEM
 // row.  KB = 64 or 32 (narrow x blocks): columns of KB digits whose 128-row
 // windows overlap, S = 128 / KB rows per coefficient (below).  Shared memory:
-// x, the zero core matrices, two Hankel buffers, the column-sum transpose
-// area (32 columns, then S - 1 columns carried from the previous 32), the
-// high words of the tile's limbs.
+// x, the zero core matrices, two Hankel buffers, the Hankel staging run,
+// the column-sum transpose area (32 columns, then S - 1 columns carried from
+// the previous 32) and the high words of the tile's limbs.  The last two
+// are live only between a tile's last drain and the next tile's first
+// Hankel build, when no MMA reads the Hankel buffers: with KB = 128 they
+// share those buffers' memory where it is large enough (a 512-limb product
+// then fits four CTAs per SM instead of three); otherwise the staging run
+// lies in the transpose area, which is free while a tile's groups run.
 template <int NT, int G, bool XC = true, int KB = 128>
 __host__ __device__ inline Layout layout(int nx, int ny) {
   static_assert(KB == 128 || KB == 64 || KB == 32, "x blocks of 128, 64 or 32 digits");
@@ -141,9 +149,18 @@ __host__ __device__ inline Layout layout(int nx, int ny) {
   L.z = (uint32_t)L.ptot * 16u * R;
   L.h0 = L.z + ZB * 128;
   L.h1 = L.h0 + HB * 128;
-  L.cs = L.h1 + HB * 128;
-  L.his = L.cs + (32 + S - 1) * 128 * 4;
-  L.total = L.his + NT * R * 4;
+  const uint32_t cs_bytes = (32 + S - 1) * 128 * 4, his_bytes = NT * R * 4;
+  if (S == 1 && cs_bytes + his_bytes <= 2u * HB * 128) {
+    L.cs = L.h0;
+    L.his = L.h0 + cs_bytes;
+    L.st = L.h1 + HB * 128;
+    L.total = L.st + 2 * hank_stage_words<G, KB>() * 4;
+  } else {
+    L.cs = L.h1 + HB * 128;
+    L.st = L.cs;
+    L.his = L.cs + cs_bytes;
+    L.total = L.his + his_bytes;
+  }
   return L;
 }
 
@@ -381,8 +398,6 @@ __device__ __forceinline__ HankLimbs hank_load(const uint64_t *y, int ny, int eb
   return v;
 }
 
-template <int G, int KB = 128>
-__host__ __device__ constexpr int hank_stage_words() { return 4 * hankel_blocks(G, KB) + 20; }
 
 template <int G, int NTH, int KB = 128>
 __device__ __forceinline__ void hank_build(uint8_t *hb, uint8_t *st, HankLimbs v, int t) {
@@ -654,7 +669,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
     if (NG > 0) {
       if (worker)
         hank_build<G, DRAIN, KB>(
-            sm + Ly.h0, sm + Ly.cs,
+            sm + Ly.h0, sm + Ly.st,
             hank_load<G, KB>(y, ny, e_lo + G - 1 < e_hi ? e_lo + G - 1 : e_hi, tid), tid);
       fence_async_smem();
       __syncthreads();
@@ -686,7 +701,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
           group_span<KB>(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
           if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
         }
-        if (more) hank_build<G, DRAIN, KB>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
+        if (more) hank_build<G, DRAIN, KB>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.st, hv, tid);
         tc_fence_before();
         fence_async_smem();
         if (__syncthreads_or(bad)) { c.aborted = true; return false; }
@@ -847,7 +862,7 @@ __device__ bool tc_partial(TcCtx &c, const uint64_t *x, int nx, const uint64_t *
     reinterpret_cast<uint4 *>(sm + Ly.z)[i] = make_uint4(0u, 0u, 0u, 0u);
   fill_x<true>(sm + Ly.xs, x, nx, Ly.ptot);
   auto last_block = [&](int gi) { return e_lo + gi * G + G - 1 < e_hi ? e_lo + gi * G + G - 1 : e_hi; };
-  if (worker) hank_build<G, DRAIN>(sm + Ly.h0, sm + Ly.cs, hank_load<G>(y, ny, last_block(g0), tid), tid);
+  if (worker) hank_build<G, DRAIN>(sm + Ly.h0, sm + Ly.st, hank_load<G>(y, ny, last_block(g0), tid), tid);
   fence_async_smem();
   __syncthreads();
   bool bad = false;
@@ -874,7 +889,7 @@ __device__ bool tc_partial(TcCtx &c, const uint64_t *x, int nx, const uint64_t *
       group_span(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
       if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
     }
-    if (more) hank_build<G, DRAIN>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.cs, hv, tid);
+    if (more) hank_build<G, DRAIN>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.st, hv, tid);
     tc_fence_before();
     fence_async_smem();
     if (__syncthreads_or(bad)) { c.aborted = true; return false; }
