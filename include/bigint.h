@@ -437,6 +437,9 @@ int bigint_host_sync(void);
  *   variant 9: integer product, 28-bit digits, 8-column chunks
  *   variant 10: one level of Karatsuba (square full products of at least 64
  *   limbs; otherwise variant 8) over variant 8's half products
+ *   variant 11: one warp per instance, 128-bit column sums (operands of at
+ *   most 64 limbs; otherwise variant 9) -- what the products inside
+ *   step-batched divisions use for operands of at most 64 limbs
  *   variant 12: the tensor-core product -- the digit convolution of the
  *   schoolbook product (Sec. V-B) as fp16 matrix products (tcgen05.mma)
  *   over signed base-256 digits with exact fp32 accumulation -- with its

@@ -221,4 +221,86 @@ __device__ __forceinline__ int blk_cmp(const uint64_t *x, const uint64_t *y, int
   return x[top - 1] > y[top - 1] ? 1 : -1;
 }
 
+// ---------------------------------------------------------------------------
+// One warp per instance.  warp_addsub: r = x +- y (+- cin) over n limbs in
+// rounds of 32, the carry of each round from two ballots (the scan of Fig.
+// 3, as blk_addsub does across a CTA).  Every lane of the warp calls it.
+// ---------------------------------------------------------------------------
+template <bool SUB, class Load, class Store>
+__device__ __forceinline__ void warp_addsub(int n, uint32_t cin, Load load, Store store) {
+  const uint32_t lane = lane_id();
+  uint32_t c = cin;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + (int)lane;
+    uint32_t g = 0, pr = 1;
+    uint64_t t = 0;
+    if (j < n) {
+      const ulonglong2 xy = load(j);
+      t = SUB ? xy.x - xy.y : xy.x + xy.y;
+      g = SUB ? (xy.x < xy.y) : (t < xy.x);
+      pr = SUB ? (t == 0) : (t == ~0ull);
+    }
+    const uint64_t cm = warp_carries(warp_gp(g, pr), c);
+    const uint32_t cl = (uint32_t)(cm >> lane) & 1u;
+    if (j < n) store(j, SUB ? t - cl : t + cl);
+    c = (uint32_t)(cm >> 32) & 1u;
+  }
+}
+
+// out[0..nout) = low nout limbs of x y (x, y, out in shared memory, cs
+// room for nout columns of 3 words), by one warp: each lane forms whole
+// columns of the schoolbook product (column j = sum_i x_i y_(j-i), 128-bit
+// limb products summed into lo + hi B + top B^2, two partial sums in
+// flight), then the columns' words are added as three shifted numbers --
+// lo, hi one limb up, top two limbs up -- with the warp carry scan.
+__device__ __forceinline__ void warp_mul(const uint64_t *x, int nx, const uint64_t *y, int ny,
+                                         uint64_t *out, int nout, uint64_t *cs) {
+  const int lane = (int)lane_id();
+  for (int j = lane; j < nout; j += 32) {
+    uint64_t lo0 = 0, hi0 = 0, top0 = 0, lo1 = 0, hi1 = 0, top1 = 0;
+    const int i0 = j - ny + 1 > 0 ? j - ny + 1 : 0, i1 = j < nx - 1 ? j : nx - 1;
+    int i = i0;
+    for (; i + 1 <= i1; i += 2) {
+      const uint64_t p0 = x[i], q0 = y[j - i], p1 = x[i + 1], q1 = y[j - i - 1];
+      const uint64_t l0 = p0 * q0, h0 = __umul64hi(p0, q0);
+      const uint64_t l1 = p1 * q1, h1 = __umul64hi(p1, q1);
+      lo0 += l0;
+      const uint64_t u0 = h0 + (lo0 < l0);  // h <= 2^64 - 2: no overflow
+      hi0 += u0;
+      top0 += hi0 < u0;
+      lo1 += l1;
+      const uint64_t u1 = h1 + (lo1 < l1);
+      hi1 += u1;
+      top1 += hi1 < u1;
+    }
+    if (i <= i1) {
+      const uint64_t p = x[i], q = y[j - i];
+      const uint64_t l = p * q, h = __umul64hi(p, q);
+      lo0 += l;
+      const uint64_t u = h + (lo0 < l);
+      hi0 += u;
+      top0 += hi0 < u;
+    }
+    lo0 += lo1;
+    const uint64_t u = hi1 + (lo0 < lo1);
+    const uint64_t carry_u = u < hi1;  // hi1 + 1 overflowed
+    hi0 += u;
+    top0 += top1 + carry_u + (hi0 < u);
+    cs[3 * j] = lo0;
+    cs[3 * j + 1] = hi0;
+    cs[3 * j + 2] = top0;
+  }
+  __syncwarp();
+  // lo + hi B (each column's hi one limb up), into the lo words
+  warp_addsub<false>(nout, 0u,
+                     [&](int j) { return make_ulonglong2(cs[3 * j], j >= 1 ? cs[3 * j - 2] : 0ull); },
+                     [&](int j, uint64_t v) { cs[3 * j] = v; });
+  __syncwarp();
+  // + top B^2
+  warp_addsub<false>(nout, 0u,
+                     [&](int j) { return make_ulonglong2(cs[3 * j], j >= 2 ? cs[3 * j - 4] : 0ull); },
+                     [&](int j, uint64_t v) { out[j] = v; });
+  __syncwarp();
+}
+
 }  // namespace bigint

@@ -32,7 +32,11 @@
 // within a few units of B^(k+l+m) / v, and since m <= l - 2 the Newton error
 // squared stays below a unit: the error does not grow from step to step.
 // Then q^ = floor(u w / B^h) (banded from limb h - 2), r^ = u - q^ v modulo
-// B^(nv+1), and the exact correction of divmod.cu settles q and r.
+// B^(nv+1), and the exact correction of divmod.cu settles q and r.  The
+// leading steps whose operands all have at most 136 limbs run in one
+// launch, a warp per instance (k_ds_small), instead of four launches each.
+#include <algorithm>
+
 #include "divcore.cuh"
 
 namespace bigint {
@@ -100,34 +104,78 @@ __global__ void k_ds_start(const uint64_t *__restrict__ U, const uint64_t *__res
   for (int jj = 0; jj < l + 2; jj++) w[jj] = jj < nq ? Qt[jj] : 0;
 }
 
-// ---------------------------------------------------------------------------
-// Per-instance linear steps with one warp per instance: r = x +- y (+- cin)
-// over n limbs in rounds of 32, the carry of each round from two ballots
-// (the scan of Fig. 3, as blk_addsub does across a CTA).  Every lane of the
-// warp calls it.
-// ---------------------------------------------------------------------------
-template <bool SUB, class Load, class Store>
-__device__ __forceinline__ void warp_addsub(int n, uint32_t cin, Load load, Store store) {
-  const uint32_t lane = lane_id();
-  uint32_t c = cin;
-  for (int base = 0; base < n; base += 32) {
-    const int j = base + (int)lane;
-    uint32_t g = 0, pr = 1;
-    uint64_t t = 0;
-    if (j < n) {
-      const ulonglong2 xy = load(j);
-      t = SUB ? xy.x - xy.y : xy.x + xy.y;
-      g = SUB ? (xy.x < xy.y) : (t < xy.x);
-      pr = SUB ? (t == 0) : (t == ~0ull);
-    }
-    const uint64_t cm = warp_carries(warp_gp(g, pr), c);
-    const uint32_t cl = (uint32_t)(cm >> lane) & 1u;
-    if (j < n) store(j, SUB ? t - cl : t + cl);
-    c = (uint32_t)(cm >> 32) & 1u;
-  }
-}
-
 constexpr int WARP_CTA = 256;  // warp-per-instance kernels: 8 instances per CTA
+
+// ---------------------------------------------------------------------------
+// The early Newton steps, while every operand of a step has at most
+// SMALL_STEP_LIMBS limbs, in one launch with one warp per instance: each
+// such step is four small launches otherwise (P, |d|, P2, update), whose
+// fixed costs are most of their time.  Per step the warp keeps w, vt, P /
+// |d| and P2 in shared memory and runs the same arithmetic as the batched
+// kernels, except that P2 = w |d| is computed whole (so floor(P2 / B^s) is
+// exact, which the step allows).
+// ---------------------------------------------------------------------------
+constexpr int SMALL_STEP_LIMBS = 136, SMALL_STEP_WARPS = 4, SMALL_STEP_MAX = 16;
+
+// The steps the fused kernel runs: (l, m, t) of each; N bounds their
+// operands (limbs, a multiple of 8): a warp's shared memory holds two
+// iterates (N each), vt and |d| (N each), P2 (2 N) and the column sums
+// (2 N x 3 words).
+struct SmallSteps {
+  int n, N;
+  int l[SMALL_STEP_MAX], m[SMALL_STEP_MAX], t[SMALL_STEP_MAX];
+};
+__host__ __device__ constexpr int small_step_warp_limbs(int N) { return 2 * N + 2 * N + 2 * N + 6 * N; }
+
+// Steps S of every instance: the iterate from W0 (its first l + 2 limbs),
+// the result (l + m + 2 limbs of the last step) to W0 or W1 as the batched
+// steps would leave it (W0 after an even number of steps).
+__global__ void __launch_bounds__(32 * SMALL_STEP_WARPS)
+    k_ds_small(const uint64_t *__restrict__ V, int nv, uint64_t *W0, uint64_t *W1, int64_t sw,
+               int64_t count, SmallSteps S) {
+  extern __shared__ __align__(16) uint64_t ssm[];
+  const int wi = threadIdx.x >> 5, lane = (int)lane_id();
+  const int64_t i = (int64_t)blockIdx.x * SMALL_STEP_WARPS + wi;
+  if (i >= count) return;  // the whole warp: no block barrier below
+  const int N = S.N;
+  uint64_t *base = ssm + (size_t)wi * small_step_warp_limbs(N);
+  uint64_t *wb[2] = {base, base + N}, *vts = base + 2 * N, *d = base + 3 * N;
+  uint64_t *z = base + 4 * N, *cs = base + 6 * N;
+  const uint64_t *v = V + i * nv;
+  const int k = nv - 1;
+  for (int j = lane; j < S.l[0] + 2; j += 32) wb[0][j] = W0[i * sw + j];
+  int cur = 0;
+  for (int st = 0; st < S.n; st++) {
+    const int l = S.l[st], m = S.m[st], t = S.t[st];
+    const int nw = l + 2, nl = t + 2;
+    uint64_t *w = wb[cur], *wn = wb[cur ^ 1];
+    for (int j = lane; j <= t; j += 32) vts[j] = v[k - t + j];
+    __syncwarp();
+    // P = vt w mod B^(t+2); |d| = P (top bit clear: d <= 0) or B^(t+2) - P
+    warp_mul(vts, t + 1, w, nw, d, nl, cs);
+    const bool ng = (d[nl - 1] >> 63) == 0;
+    if (!ng) {
+      warp_addsub<true>(nl, 0u, [&](int j) { return make_ulonglong2(0ull, d[j]); },
+                        [&](int j, uint64_t x) { d[j] = x; });
+      __syncwarp();
+    }
+    // P2 = w |d| (whole); w' = w B^m + floor(P2 / B^s) or w B^m - floor(P2 / B^s) - 1
+    warp_mul(w, nw, d, nl, z, nw + nl, cs);
+    const int s = t + l - m, ny = nw + nl - s;
+    auto load = [&](int j) {
+      const uint64_t x = (j >= m && j - m < nw) ? w[j - m] : 0ull;
+      return make_ulonglong2(x, j < ny ? z[s + j] : 0ull);
+    };
+    auto store = [&](int j, uint64_t x) { wn[j] = x; };
+    if (ng) warp_addsub<true>(l + m + 2, 1u, load, store);
+    else warp_addsub<false>(l + m + 2, 0u, load, store);
+    __syncwarp();
+    cur ^= 1;
+  }
+  const int nlast = S.l[S.n - 1] + S.m[S.n - 1] + 2;
+  uint64_t *out = (S.n & 1) ? W1 : W0;
+  for (int j = lane; j < nlast; j += 32) out[i * sw + j] = wb[cur][j];
+}
 
 // One warp per instance: the sign of d from P = vt w mod B^nl and |d| (nl
 // limbs): P itself if its top bit is clear (d <= 0), else B^nl - P.
@@ -350,7 +398,36 @@ int launch_divmod_steps(const uint64_t *u, const uint64_t *v, uint64_t *q, uint6
   if (rc != BIGINT_OK) return rc;
   int cur = 0;
   const unsigned gw = (unsigned)((count + WARP_CTA / 32 - 1) / (WARP_CTA / 32));
-  for (int i = 0; i < ns; i++) {
+  // the leading steps whose operands are all small, fused into one launch
+  SmallSteps SS;
+  SS.n = 0;
+  SS.N = 8;
+  while (SS.n < ns && SS.n < SMALL_STEP_MAX) {
+    const Step &S0 = steps[SS.n];
+    // every operand and result of the step within N limbs (w' too)
+    const int need = std::max(std::max(S0.l + 2, S0.t + 2), S0.l + S0.m + 2);
+    if (need > SMALL_STEP_LIMBS) break;
+    SS.N = std::max(SS.N, (need + 7) / 8 * 8);
+    SS.l[SS.n] = S0.l;
+    SS.m[SS.n] = S0.m;
+    SS.t[SS.n] = S0.t;
+    SS.n++;
+  }
+  if (SS.n > 0) {
+    const size_t smem = (size_t)8 * SMALL_STEP_WARPS * small_step_warp_limbs(SS.N);
+    static bool attr = false;
+    if (!attr) {
+      BIGINT_CUDA_TRY(cudaFuncSetAttribute(
+          k_ds_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          8 * SMALL_STEP_WARPS * small_step_warp_limbs(SMALL_STEP_LIMBS)));
+      attr = true;
+    }
+    k_ds_small<<<(unsigned)((count + SMALL_STEP_WARPS - 1) / SMALL_STEP_WARPS),
+                 32 * SMALL_STEP_WARPS, smem, st>>>(v, nv, W[0], W[1], Y.sw, count, SS);
+    if ((rc = bigint_launch_status()) != BIGINT_OK) return rc;
+    cur = SS.n & 1;
+  }
+  for (int i = SS.n; i < ns; i++) {
     const Step S = steps[i];
     const int nw = S.l + 2, nl = S.t + 2;
     // P = vt w mod B^(t+2)

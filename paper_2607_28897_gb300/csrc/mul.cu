@@ -20,6 +20,43 @@ __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
   blk_mul<RB, Q, F>(A + inst * sa, na, Bm + inst * sb, nb, Out + inst * so, nout, smem);
 }
 
+// ---- small products, one warp each -------------------------------------------
+// Products whose operands have at most SMALL_LIMBS limbs, thousands at a
+// time: a CTA per instance (blk_mul) spends most of such a launch on its
+// fixed costs, so here one warp takes an instance and runs warp_mul
+// (blockops.cuh: whole schoolbook columns per lane, then the carry scan).
+// Exact low nout limbs (nout <= na + nb).
+constexpr int SMALL_LIMBS = 64, SMALL_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * SMALL_WARPS)
+    k_mul_small(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
+                uint64_t *__restrict__ Out, int na, int nb, int nout, int64_t count, int64_t sa,
+                int64_t sb, int64_t so) {
+  __shared__ uint64_t xs[SMALL_WARPS][SMALL_LIMBS], ys[SMALL_WARPS][SMALL_LIMBS];
+  __shared__ uint64_t os[SMALL_WARPS][2 * SMALL_LIMBS], cs[SMALL_WARPS][6 * SMALL_LIMBS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t inst = (int64_t)blockIdx.x * SMALL_WARPS + w;
+  if (inst >= count) return;  // the whole warp: no block barrier below
+  const uint64_t *a = A + inst * sa, *b = Bm + inst * sb;
+  for (int i = lane; i < na; i += 32) xs[w][i] = a[i];
+  for (int i = lane; i < nb; i += 32) ys[w][i] = b[i];
+  __syncwarp();
+  warp_mul(xs[w], na, ys[w], nb, os[w], nout, cs[w]);
+  uint64_t *o = Out + inst * so;
+  for (int j = lane; j < nout; j += 32) o[j] = os[w][j];
+}
+
+static int launch_mul_small(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb,
+                            uint64_t *out, int64_t so, int64_t count, int na, int nb, int nout,
+                            cudaStream_t st) {
+  if (na > SMALL_LIMBS || nb > SMALL_LIMBS || nout > na + nb) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  const int64_t blocks = (count + SMALL_WARPS - 1) / SMALL_WARPS;
+  k_mul_small<<<(unsigned)blocks, 32 * SMALL_WARPS, 0, st>>>(a, b, out, na, nb, nout, count, sa,
+                                                             sb, so);
+  return bigint_launch_status();
+}
+
 template <int RB, int Q, int F>
 __global__ void __launch_bounds__(Q >= 16 ? 640 : 1024)
     k_mul_kara(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
@@ -128,7 +165,7 @@ int mul_size_class(int na, int nb) {
 }
 
 bool mul_variant_valid(int v) {
-  return v == 0 || v == 8 || v == 9 || v == 10 || (v >= 12 && v <= 17);
+  return v == 0 || (v >= 8 && v <= 17);
 }
 
 int mul_set_variant(int v) {
@@ -153,6 +190,7 @@ int mul_variant_for(int na, int nb, int nout) {
   }
   const bool square_full = na == nb && nout == na + nb && na >= 64;
   if (v == 10 && !square_full) v = 8;                // Karatsuba: square full products only
+  if (v == 11 && (na > SMALL_LIMBS || nb > SMALL_LIMBS)) v = 9;  // warp per instance: small only
   if (v >= 12 && mul_tc_smem(na, nb) == 0) v = 8;    // tensor-core product: shared memory bound
   return v;
 }
@@ -168,6 +206,7 @@ int launch_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t coun
     case 16: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_N64);
     case 17: return launch_mul_tc(a, b, out, count, na, nb, nout, st, TC_FORCE_N32);
     case 10: return launch_kara<29, 16, 32>(a, b, out, count, na, st);
+    case 11: return launch_mul_small(a, na, b, nb, out, nout, count, na, nb, nout, st);
     case 9: return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st);
     default: return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st);
   }
@@ -207,6 +246,7 @@ int launch_mul_ex(const uint64_t *a, int64_t sa, const uint64_t *b, int64_t sb, 
     }
   }
   const int nmax = na > nb ? na : nb;
+  if (nmax <= SMALL_LIMBS) return launch_mul_small(a, sa, b, sb, out, so, count, na, nb, nout, st);
   if (nmax < 1536) return launch_variant<28, 8, 128>(a, b, out, count, na, nb, nout, st, sa, sb, so);
   return launch_variant<29, 16, 32>(a, b, out, count, na, nb, nout, st, sa, sb, so);
 }

@@ -87,7 +87,7 @@ def test_config_sweep_full_size(bi, orc, n):
     assert np.array_equal(p[idx], orc.batch_mul(a[idx], b[idx]))
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10, 12, 13, 14, 15, 16, 17])
+@pytest.mark.parametrize("variant", [8, 9, 10, 11, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("n", [1, 63, 64, 65, 511, 1000, 2049])
 def test_every_variant(bi, orc, variant, n):
     """Every multiply variant (integer digit size and chunk width, Karatsuba,
@@ -105,3 +105,25 @@ def test_every_variant(bi, orc, variant, n):
     finally:
         bi.set_variant(0, 0)
     assert np.array_equal(p, orc.batch_mul(a, b))
+
+
+@pytest.mark.parametrize("na,nb,m", [(1, 1, 2), (1, 64, 65), (64, 1, 3), (2, 3, 5), (17, 33, 50),
+                                     (33, 17, 20), (64, 64, 128), (64, 64, 1), (31, 32, 40),
+                                     (64, 63, 66), (5, 64, 69)])
+def test_warp_per_instance_products(bi, orc, na, nb, m):
+    """Variant 11 (one warp per instance, operands of at most 64 limbs): full
+    and low products of ragged shapes, more instances than warps of one
+    CTA, all-ones operands (every column sum at its largest)."""
+    from paper_2607_28897_gb300 import inputs
+
+    a = inputs.limbs(60 + na, 21, na)
+    b = inputs.limbs(61 + nb, 21, nb)
+    a[::5] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    b[::5] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    bi.set_variant(0, 11)
+    try:
+        got = to_host(bi.mul_lo(to_dev(a), to_dev(b), m))
+    finally:
+        bi.set_variant(0, 0)
+    want = np.stack([orc.mul_lo(a[i], b[i], m) for i in range(a.shape[0])])
+    assert np.array_equal(got, want)
