@@ -368,7 +368,9 @@ int bigint_load_tuning(const char *path);
  * bigint_poly: out = (a a + b)(b b + b) + a b mod B^n (Table II's Poly: four
  * multiplications, three additions, every value kept to n limbs as the
  * paper's same-width multiply and add).  One persistent launch; products of
- * n >= 256 limbs run on the tensor cores; intermediates live in `workspace`
+ * n >= 256 limbs run on the tensor cores, with the smallest tile that holds
+ * a low n x n product's n / 16 columns (up to four CTAs per SM for n <=
+ * 1024, two up to 2048, one above); intermediates live in `workspace`
  * (device memory of bigint_poly_workspace(count, n) bytes: 3 n limbs per
  * resident CTA, small enough to stay in L2).  a, b, out: count x n limbs,
  * out disjoint from a and b.  n <= BIGINT_MUL_MAX_LIMBS.

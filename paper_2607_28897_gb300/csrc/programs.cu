@@ -93,22 +93,24 @@ __global__ void __launch_bounds__(1024)
 
 // ---------------------------------------------------------------------------
 // Poly: persistent CTAs; per instance four low-part products (tensor cores
-// when n >= TC_DIV_MIN, else blk_mul) and three in-place additions through a
-// per-CTA scratch of 3n limbs.
+// when n >= TC_DIV_MIN, with the tile of NT columns that holds the n / 16
+// columns of a low n x n product, so that small programs run several CTAs
+// per SM; else blk_mul) and three in-place additions through a per-CTA
+// scratch of 3n limbs.
 // ---------------------------------------------------------------------------
-template <bool TC, int G>
-__global__ void __launch_bounds__(TC ? tcm::TC_CTA_THREADS : 512, 1)
+template <bool TC, int NT, int G>
+__global__ void __launch_bounds__(TC ? 2 * NT + 32 : 512, TC ? 256 / NT : 1)
     k_poly(const uint64_t *__restrict__ A, const uint64_t *__restrict__ Bm,
            uint64_t *__restrict__ Out, int n, int64_t count, uint64_t *scratch, int smem_words) {
   extern __shared__ __align__(1024) uint32_t smem[];
   __shared__ uint32_t scr[BLK_SCRATCH_WORDS];
   __shared__ tcm::TcShared tsh;
   tcm::TcCtx tcc;
-  if constexpr (TC) tcm::tc_init<256>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
+  if constexpr (TC) tcm::tc_init<NT>(tcc, reinterpret_cast<uint8_t *>(smem), &tsh, scr);
   uint64_t *T1 = scratch + (int64_t)blockIdx.x * 3 * n, *T2 = T1 + n, *T3 = T2 + n;
   auto prod = [&](const uint64_t *x, const uint64_t *y, uint64_t *out) {
     if constexpr (TC) {
-      tcm::tc_product<256, G, true>(tcc, x, n, y, n, out, n, 0);
+      tcm::tc_product<NT, G, true>(tcc, x, n, y, n, out, n, 0);
     } else {
       blk_mul_call<divc::DRB, divc::DQ, divc::DF>(x, n, y, n, out, n, smem, 0);
     }
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(TC ? tcm::TC_CTA_THREADS : 512, 1)
       if (tcc.aborted) break;
     }
   }
-  if constexpr (TC) tcm::tc_release<256>(tcc);
+  if constexpr (TC) tcm::tc_release<NT>(tcc);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,7 +156,7 @@ int launch_add_chain(const uint64_t *a, const uint64_t *b, uint64_t *out, uint8_
 
 namespace {
 
-template <bool TC, int G>
+template <bool TC, int NT, int G>
 int poly_dyn_max() {
   static int dyn = -1;
   if (dyn < 0) {
@@ -163,13 +165,32 @@ int poly_dyn_max() {
     BIGINT_CUDA_TRY(
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa;
-    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_poly<TC, G>));
+    BIGINT_CUDA_TRY(cudaFuncGetAttributes(&fa, k_poly<TC, NT, G>));
     const int d = optin - (int)fa.sharedSizeBytes;
-    BIGINT_CUDA_TRY(
-        cudaFuncSetAttribute(k_poly<TC, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
+    BIGINT_CUDA_TRY(cudaFuncSetAttribute(k_poly<TC, NT, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, d));
     dyn = d;
   }
   return dyn;
+}
+
+// CTAs of k_poly<TC, NT, G> resident on one SM with `smem` bytes of dynamic
+// shared memory (the tensor memory allows 256 / NT of them), 0 on error.
+template <bool TC, int NT, int G>
+int poly_per_sm(size_t smem) {
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+          cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_poly<TC, NT, G>) != cudaSuccess) return 0;
+  int per = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+  const int cap = TC ? 256 / NT : 1;
+  if (per > cap) per = cap;
+  return per < 1 ? 1 : per;
 }
 
 int sm_count(int *sms) {
@@ -179,18 +200,49 @@ int sm_count(int *sms) {
   return BIGINT_OK;
 }
 
-template <bool TC, int G>
-int launch_poly_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
-                        void *ws, size_t bytes, size_t need, cudaStream_t st) {
-  const int dyn = poly_dyn_max<TC, G>();
-  if (dyn <= 0 || need > (size_t)dyn) return BIGINT_EINVAL;
+// The launch of Poly for n-limb operands: which k_poly, its dynamic shared
+// memory and CTAs per SM.  Tensor cores from TC_DIV_MIN limbs with the
+// smallest tile holding the n / 16 columns of a low n x n product.
+struct PolyPlan {
+  int form;  // 0: integer, 1: NT 64, 2: NT 128, 3: NT 256 G 8, 4: NT 256 G 4
+  size_t smem;
+  int per_sm;
+};
+
+template <bool TC, int NT, int G>
+bool poly_try(int form, size_t smem, PolyPlan &P) {
+  const int dyn = poly_dyn_max<TC, NT, G>();
+  if (dyn <= 0 || smem > (size_t)dyn) return false;
+  P.form = form;
+  P.smem = smem;
+  P.per_sm = poly_per_sm<TC, NT, G>(smem);
+  return P.per_sm > 0;
+}
+
+bool poly_plan(int n, PolyPlan &P) {
+  if (n >= divc::TC_DIV_MIN) {
+    const int cols = (n + 15) / 16;
+    if (cols <= 64 && poly_try<true, 64, 7>(1, tcm::layout<64, 7>(n, n).total, P)) return true;
+    if (cols <= 128 && poly_try<true, 128, 8>(2, tcm::layout<128, 8>(n, n).total, P)) return true;
+    if (poly_try<true, 256, 8>(3, tcm::layout<256, 8>(n, n).total, P)) return true;
+    if (poly_try<true, 256, 4>(4, tcm::layout<256, 4>(n, n).total, P)) return true;
+  }
+  return poly_try<false, 256, 8>(0, 4 * (size_t)blk_mul_smem_words<divc::DRB, divc::DQ>(n, n),
+                                 P);
+}
+
+int64_t poly_grid(const PolyPlan &P, int64_t count) {
   int sms = 0;
-  const int rc = sm_count(&sms);
-  if (rc != BIGINT_OK) return rc;
-  const int64_t grid = count < sms ? count : sms;
-  if (bytes < (size_t)grid * 3 * n * 8) return BIGINT_ENOMEM;
-  k_poly<TC, G><<<(unsigned)grid, TC ? tcm::TC_CTA_THREADS : 512, need, st>>>(a, b, out, n, count,
-                                                   static_cast<uint64_t *>(ws), (int)(need / 4));
+  if (sm_count(&sms) != BIGINT_OK) return 0;
+  const int64_t slots = (int64_t)sms * P.per_sm;
+  return count < slots ? count : slots;
+}
+
+template <bool TC, int NT, int G>
+int launch_poly_variant(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                        void *ws, int64_t grid, size_t smem, cudaStream_t st) {
+  k_poly<TC, NT, G><<<(unsigned)grid, TC ? 2 * NT + 32 : 512, smem, st>>>(
+      a, b, out, n, count, static_cast<uint64_t *>(ws), (int)(smem / 4));
   return bigint_launch_status();
 }
 
@@ -202,23 +254,27 @@ int programs_take_timeout() { return tcm::take_timeout_here(); }
 int programs_set_wait_limit(long long cycles) { return tcm::set_wait_limit_here(cycles); }
 
 size_t poly_workspace(int64_t count, int n) {
-  int sms = 0;
-  if (sm_count(&sms) != BIGINT_OK) return 0;
-  const int64_t grid = count < sms ? count : sms;
+  PolyPlan P;
+  if (n < 1 || !poly_plan(n, P)) return 0;
+  const int64_t grid = poly_grid(P, count);
   return (size_t)(grid > 0 ? grid : 1) * 3 * (size_t)n * 8;
 }
 
 int launch_poly(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
                 void *ws, size_t bytes, cudaStream_t st) {
   if (count == 0) return BIGINT_OK;
-  if (n >= divc::TC_DIV_MIN) {
-    const size_t n8 = tcm::layout<256, 8>(n, n).total, n4 = tcm::layout<256, 4>(n, n).total;
-    if (poly_dyn_max<true, 8>() > 0 && n8 <= (size_t)poly_dyn_max<true, 8>())
-      return launch_poly_variant<true, 8>(a, b, out, count, n, ws, bytes, n8, st);
-    return launch_poly_variant<true, 4>(a, b, out, count, n, ws, bytes, n4, st);
+  PolyPlan P;
+  if (!poly_plan(n, P)) return BIGINT_EINVAL;
+  const int64_t grid = poly_grid(P, count);
+  if (grid <= 0) return BIGINT_ECUDA;
+  if (bytes < (size_t)grid * 3 * n * 8) return BIGINT_ENOMEM;
+  switch (P.form) {
+    case 1: return launch_poly_variant<true, 64, 7>(a, b, out, count, n, ws, grid, P.smem, st);
+    case 2: return launch_poly_variant<true, 128, 8>(a, b, out, count, n, ws, grid, P.smem, st);
+    case 3: return launch_poly_variant<true, 256, 8>(a, b, out, count, n, ws, grid, P.smem, st);
+    case 4: return launch_poly_variant<true, 256, 4>(a, b, out, count, n, ws, grid, P.smem, st);
+    default: return launch_poly_variant<false, 256, 8>(a, b, out, count, n, ws, grid, P.smem, st);
   }
-  const size_t need = 4 * (size_t)blk_mul_smem_words<divc::DRB, divc::DQ>(n, n);
-  return launch_poly_variant<false, 8>(a, b, out, count, n, ws, bytes, need, st);
 }
 
 }  // namespace bigint

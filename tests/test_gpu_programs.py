@@ -39,7 +39,7 @@ def test_add_chain(bi, orc, n, k):
         assert int(carry[i]) == c, i
 
 
-@pytest.mark.parametrize("n", [1, 5, 100, 255, 256, 300, 1024, 2048, 4096])
+@pytest.mark.parametrize("n", [1, 5, 100, 255, 256, 300, 512, 1024, 1025, 2048, 2049, 4096])
 def test_poly(bi, orc, n):
     from paper_2607_28897_gb300 import inputs
 
@@ -54,12 +54,13 @@ def test_poly(bi, orc, n):
 
 
 def test_poly_many_instances(bi, orc):
-    """More instances than resident CTAs: the per-CTA scratch is reused."""
+    """More instances than resident CTAs (four per SM with the 64-column
+    tile): the per-CTA scratch is reused."""
     from paper_2607_28897_gb300 import inputs
 
-    n, count = 384, 400
+    n, count = 384, 1500
     a = inputs.limbs(901, count, n)
     b = inputs.limbs(902, count, n)
     out = to_host(bi.poly(to_dev(a), to_dev(b)))
-    for i in (0, 1, 151, 152, 153, 399):
+    for i in (0, 1, 151, 152, 153, 607, 608, 609, 1216, 1499):
         assert np.array_equal(out[i], orc.poly(a[i], b[i])), i
