@@ -119,6 +119,26 @@ int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out,
                      int64_t count, int32_t na, int32_t nb, void *workspace,
                      size_t workspace_bytes, void *stream);
 
+/* ---- sub-quadratic full products (Karatsuba over the products above) -----
+ * out = a * b for square operands (a, b: count x n limbs, out: count x 2n,
+ * disjoint from a and b), by `levels` levels of Karatsuba's method in its
+ * subtractive form -- x y = z2 B^2k + (z0 + z2 + (x0 - x1)(y1 - y0)) B^k +
+ * z0 with n = 2k -- every step batched across the instances, the leaf
+ * products those of bigint_mul (tensor cores from 256 limbs).  The paper
+ * names sub-quadratic multiplication as its next step; this is its exact
+ * integer form.  levels: 0..3, or -1 for the measured choice on GB300 (two
+ * from 8192 limbs, one from 4096, none below); a level that would not halve
+ * n exactly is dropped.  Bit-identical to bigint_mul.
+ * workspace: device memory, 256-byte aligned, owned by the caller, contents
+ * clobbered; bigint_mul_kara_workspace(count, n, levels) bytes run the
+ * batch in one pass, fewer run it in chunks of as many instances as fit
+ * (BIGINT_ENOMEM if not even one fits; NULL is fine when no level runs).
+ * 1 <= n <= BIGINT_MUL_MAX_LIMBS; BIGINT_EINVAL otherwise.                  */
+size_t bigint_mul_kara_workspace(int64_t count, int32_t n, int32_t levels);
+int bigint_mul_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count,
+                    int32_t n, int32_t levels, void *workspace, size_t workspace_bytes,
+                    void *stream);
+
 /* ---- division (Sec. V-C, Fig. 6) ----------------------------------------
  * q = floor(u / v), r = u - q v, by the shifted inverse
  *   w = shinv_h(v) = floor(B^h / v)

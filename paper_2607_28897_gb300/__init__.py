@@ -16,6 +16,7 @@ import os
 
 __all__ = [
     "BigIntError", "load", "add", "sub", "mul", "mul_lo", "mul_split", "mul_split_workspace_bytes",
+    "mul_kara", "mul_kara_workspace_bytes",
     "divmod", "divmod_noalloc", "divmod_inv", "shinv",
     "divmod_workspace_bytes", "shinv_workspace_bytes", "probe_int_throughput", "set_variant",
     "set_wait_limit", "check_timeout",
@@ -44,6 +45,8 @@ SIGNATURES = {
     "bigint_mul": ([_P, _P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "bigint_mul_lo": ([_P, _P, _P, _I64, _I32, _I32, _I32, _P], ctypes.c_int),
     "bigint_mul_split": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
+    "bigint_mul_kara_workspace": ([_I64, _I32, _I32], ctypes.c_size_t),
+    "bigint_mul_kara": ([_P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_mul_split_workspace": ([_I64, _I32, _I32], _SZ),
     "bigint_divmod": ([_P, _P, _P, _P, _P, _I64, _I32, _I32, _P, _SZ, _P], ctypes.c_int),
     "bigint_divmod_workspace": ([_I64, _I32, _I32], _SZ),
@@ -197,6 +200,28 @@ def mul(a, b, out=None, stream=None):
     rc = load().bigint_mul(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, na, nb,
                            _stream_ptr(stream))
     _check(rc, "bigint_mul")
+    return out
+
+
+def mul_kara_workspace_bytes(count: int, n: int, levels: int = -1) -> int:
+    """Workspace bytes of bigint_mul_kara for one pass over the batch."""
+    return int(load().bigint_mul_kara_workspace(count, n, levels))
+
+
+def mul_kara(a, b, levels: int = -1, out=None, workspace=None, stream=None):
+    """Full products of square operands by Karatsuba's method over the
+    batched products (bit-identical to mul; levels -1: by size)."""
+    a, b = _dev_tensor(a, "a"), _dev_tensor(b, "b")
+    count, n = a.shape
+    if b.shape != a.shape:
+        raise BigIntError(EINVAL, "mul_kara: a and b must have the same shape")
+    out = _empty_like_limbs(a, count, 2 * n) if out is None else _dev_tensor(out, "out")
+    if workspace is None:
+        workspace = _workspace(mul_kara_workspace_bytes(count, n, levels), a.device)
+    rc = load().bigint_mul_kara(a.data_ptr(), b.data_ptr(), out.data_ptr(), count, n, levels,
+                                workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                _stream_ptr(stream))
+    _check(rc, "bigint_mul_kara")
     return out
 
 

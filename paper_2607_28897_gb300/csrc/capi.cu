@@ -21,6 +21,9 @@ int mul_max_limbs();
 size_t mul_split_workspace(int64_t count, int na, int nb);
 int launch_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int na,
                      int nb, void *ws, size_t bytes, cudaStream_t st);
+size_t mul_kara_workspace(int64_t count, int n, int levels);
+int launch_mul_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                    int levels, void *ws, size_t bytes, cudaStream_t st);
 int mul_set_variant(int v);
 int mul_variant_for(int na, int nb, int nout);
 int tc_take_timeout();
@@ -144,6 +147,19 @@ int bigint_mul_split(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_
   if (!a || !b || !out) return BIGINT_EINVAL;
   return launch_mul_split(a, b, out, count, na, nb, workspace, workspace_bytes,
                           as_stream(stream));
+}
+
+size_t bigint_mul_kara_workspace(int64_t count, int32_t n, int32_t levels) {
+  return mul_kara_workspace(count, n, levels);
+}
+
+int bigint_mul_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int32_t n,
+                    int32_t levels, void *workspace, size_t workspace_bytes, void *stream) {
+  if (count < 0 || count > 0x7fffffff || n < 1 || n > mul_max_limbs()) return BIGINT_EINVAL;
+  if (count == 0) return BIGINT_OK;
+  if (!a || !b || !out) return BIGINT_EINVAL;
+  return launch_mul_kara(a, b, out, count, n, levels, workspace, workspace_bytes,
+                         as_stream(stream));
 }
 
 int bigint_divmod_inv(const uint64_t *u, const uint64_t *v, const uint64_t *w, uint64_t *q,

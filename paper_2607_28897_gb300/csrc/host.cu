@@ -33,6 +33,10 @@ int launch_divmod(const uint64_t *u, const uint64_t *v, uint64_t *q, uint64_t *r
                   int32_t *status, int64_t count, int nu, int nv, void *ws, size_t bytes,
                   cudaStream_t st);
 size_t divmod_workspace(int64_t count, int nu, int nv);
+int kara_levels(int n, int levels);
+size_t mul_kara_workspace(int64_t count, int n, int levels);
+int launch_mul_kara(const uint64_t *a, const uint64_t *b, uint64_t *out, int64_t count, int n,
+                    int levels, void *ws, size_t bytes, cudaStream_t st);
 int mul_max_limbs();
 
 namespace {
@@ -62,6 +66,12 @@ Shape shape_of(int op, int na, int nb) {
   return s;
 }
 
+// Square products of the sizes where bigint_mul_kara's measured choice runs
+// Karatsuba levels take that form here too (with its workspace in the slot).
+bool kara_form(const Shape &s) {
+  return s.op == BIGINT_OP_MUL && s.na == s.nb && kara_levels(s.na, -1) > 0;
+}
+
 // Device bytes of one staging slot for `c` instances.
 size_t slot_bytes(const Shape &s, int64_t c) {
   size_t b = align_up(8 * (size_t)c * s.na) + align_up(8 * (size_t)c * s.nb) +
@@ -69,6 +79,7 @@ size_t slot_bytes(const Shape &s, int64_t c) {
   if (s.no1) b += align_up(8 * (size_t)c * s.no1);
   if (s.aux) b += align_up((size_t)c * s.aux);
   if (s.op == BIGINT_OP_DIVMOD) b += align_up(divmod_workspace(c, s.na, s.nb));
+  if (kara_form(s)) b += align_up(mul_kara_workspace(c, s.na, -1));
   return b;
 }
 
@@ -89,6 +100,10 @@ Slot carve_slot(const Shape &s, int64_t c, uint8_t *base) {
   if (s.op == BIGINT_OP_DIVMOD) {
     sl.ws = p;
     sl.ws_bytes = divmod_workspace(c, s.na, s.nb);
+  }
+  if (kara_form(s)) {
+    sl.ws = p;
+    sl.ws_bytes = mul_kara_workspace(c, s.na, -1);
   }
   return sl;
 }
@@ -196,7 +211,10 @@ int run(const Shape &s, const uint64_t *in0, const uint64_t *in1, uint64_t *out0
                            static_cast<uint8_t *>(sl.aux), m, s.na, p->comp);
         break;
       case BIGINT_OP_MUL:
-        rc = launch_mul(sl.in0, sl.in1, sl.out0, m, s.na, s.nb, s.na + s.nb, p->comp);
+        rc = kara_form(s) ? launch_mul_kara(sl.in0, sl.in1, sl.out0, m, s.na, -1, sl.ws,
+                                            sl.ws_bytes, p->comp)
+                          : launch_mul(sl.in0, sl.in1, sl.out0, m, s.na, s.nb, s.na + s.nb,
+                                       p->comp);
         break;
       default:
         rc = launch_divmod(sl.in0, sl.in1, sl.out0, sl.out1, static_cast<int32_t *>(sl.aux), m,

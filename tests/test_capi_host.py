@@ -207,3 +207,15 @@ def test_views_rejected_on_the_host(L):
                                  ctypes.byref(r), None, ws, 1 << 20, None) == bi.EINVAL
     assert L.bigint_batch_run(None, 3, None, None, None, ws, 0, 0, None) == bi.EINVAL
     assert L.bigint_batch_run(None, 0, None, None, None, None, 0, 9, None) == bi.EINVAL
+
+
+def test_mul_kara_checks(L):
+    """Argument checks of the Karatsuba product that need no GPU."""
+    import paper_2607_28897_gb300 as bi
+
+    P = ctypes.c_void_p(8)
+    assert L.bigint_mul_kara(P, P, P, -1, 8, 1, None, 0, None) == bi.EINVAL
+    assert L.bigint_mul_kara(P, P, P, 4, 0, 1, None, 0, None) == bi.EINVAL
+    assert L.bigint_mul_kara(P, P, P, 4, 20000, 1, None, 0, None) == bi.EINVAL
+    assert L.bigint_mul_kara(None, P, P, 4, 8, 1, None, 0, None) == bi.EINVAL
+    assert L.bigint_mul_kara(P, P, P, 0, 8, 1, None, 0, None) == bi.OK

@@ -55,6 +55,21 @@ def test_mul_host_tensor_cores(bi):
     assert np.array_equal(out, to_host(bi.mul(to_dev(a), to_dev(b))))
 
 
+def test_mul_host_karatsuba(bi, orc):
+    """Square products of 4096 and 8192 limbs take the Karatsuba form in the
+    host path (its workspace inside each staging slot): the oracle's
+    products, over several chunks."""
+    from paper_2607_28897_gb300 import inputs
+
+    for n, count in ((4096, 7), (8192, 5)):
+        a = inputs.limbs(75 + n, count, n)
+        b = inputs.limbs(76 + n, count, n)
+        a[0] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        ws = ws_for(bi, bi.OP_MUL, 2, n, n)
+        out = bi.mul_host(host(a), host(b), workspace=ws).numpy().view(np.uint64)
+        assert np.array_equal(out, orc.batch_mul(a, b)), n
+
+
 @pytest.mark.parametrize("sub", [False, True])
 def test_addsub_host(bi, orc, sub):
     import torch
