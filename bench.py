@@ -558,12 +558,21 @@ def main():
                                      "4096 and 8192 limbs run as 1 and 2 Karatsuba levels over "
                                      "2048-limb products of this kernel"),
                     "frac_of_sustained": achieved / sustained,
+                    # the sustained peak scaled from its own median SM clock to
+                    # the clock this step held (time x median SM MHz)
+                    "frac_clock_normalized": (
+                        achieved / (sustained * clk["sm_mhz"] /
+                                    float(peaks["clocks_under_load"]["sm_mhz_median"]))
+                        if clk and peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+                        else None),
                     "frac_of_nominal_2250": achieved / 2250.0,
                     "peak_basis": ("of measured: MEASURED_PEAKS.json bf16_tflops (burst: a GEMM "
                                    "timed alone; fp16 and bf16 share the nominal dense rate), "
                                    "the basis for a step that held the maximum SM clock; "
                                    "frac_of_sustained divides by bf16_tflops_sustained "
-                                   "(measured power-capped)")
+                                   "(measured power-capped), frac_clock_normalized by that "
+                                   "peak scaled by this step's median SM clock over the "
+                                   "median clock of its measurement")
                     if "bf16_tflops" in peaks else "of fallback: 1900 TFLOP/s burst"}
     else:
         ipc, probe_mhz = bi.probe_int_throughput(0)  # IMAD.WIDE per SM per clock
