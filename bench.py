@@ -360,14 +360,26 @@ def main():
 
     mul_events = {n: [] for n in sizes}
     add_events = {n: [] for n in sizes}
-    # the three divisions are independent and none fills the GPU to its end
-    # (2^20 / 2^19 bits: 256 one-SM instances, two waves on 152 SMs), so they
-    # run side by side on streams of their own, the largest first: the
-    # smaller ones take the SMs the larger ones leave idle in their last wave
+    # the three divisions are independent of the sweep and of each other, and
+    # none fills the GPU to its end (2^20 / 2^19 bits: 256 one-SM instances,
+    # two waves on 152 SMs), so they run on streams of their own from the
+    # start of the step, the largest first: their launches take the SMs the
+    # sweep's launches leave idle between kernels and in their last waves
     div_streams = [torch.cuda.Stream(device=dev) for _ in DIV]
 
     def one_step(record):
         flush.fill_(1)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        joins = []
+        for (n, batch), ds in zip(sorted(DIV, reverse=True), div_streams):
+            D = divs[n]
+            ds.wait_event(fork)
+            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"],
+                      stream=ds)
+            j = torch.cuda.Event()
+            j.record(ds)
+            joins.append(j)
         for n in sizes:
             S = sweep[n]
             if record:
@@ -387,17 +399,6 @@ def main():
                 e3 = torch.cuda.Event(enable_timing=True)
                 e3.record(stream)
                 mul_events[n].append((e2, e3))
-        fork = torch.cuda.Event()
-        fork.record(stream)
-        joins = []
-        for (n, batch), ds in zip(sorted(DIV, reverse=True), div_streams):
-            D = divs[n]
-            ds.wait_event(fork)
-            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"],
-                      stream=ds)
-            j = torch.cuda.Event()
-            j.record(ds)
-            joins.append(j)
         for j in joins:
             stream.wait_event(j)
 
@@ -446,13 +447,17 @@ def main():
     for n in sizes:
         S = sweep[n]
         b = S["a"].shape[0]
-        t_add = sum(e0.elapsed_time(e1) for e0, e1 in add_events[n]) / len(add_events[n])
-        t_mul = sum(e0.elapsed_time(e1) for e0, e1 in mul_events[n]) / len(mul_events[n])
+        # each op alone (the step's own spans share the GPU with the divisions)
+        t_add = time_op(lambda: bi.add(S["a"], S["b"], out=S["s"], carry=S["c"]))
+        t_mul = time_op(lambda: bi.mul_kara(S["a"], S["b"], out=S["p"], workspace=S["kws"]))
+        in_add = sum(e0.elapsed_time(e1) for e0, e1 in add_events[n]) / len(add_events[n])
+        in_mul = sum(e0.elapsed_time(e1) for e0, e1 in mul_events[n]) / len(mul_events[n])
         breakdown[f"add_{n}"] = {"ms": t_add, "ops_per_s": b / (t_add * 1e-3),
-                                 "GB_s": 24.0 * b * n / (t_add * 1e-3) / 1e9}
+                                 "GB_s": 24.0 * b * n / (t_add * 1e-3) / 1e9,
+                                 "in_step_ms": in_add}
         breakdown[f"mul_{n}"] = {"ms": t_mul, "ops_per_s": b / (t_mul * 1e-3),
                                  "limb_gops": b * n * n / (t_mul * 1e-3) / 1e9,
-                                 "form": kara_form(n)}
+                                 "form": kara_form(n), "in_step_ms": in_mul}
         if kara_levels(n) > 0:  # the schoolbook product alone, for the roofline
             breakdown[f"mul_{n}"]["schoolbook_ms"] = time_op(
                 lambda: bi.mul(S["a"], S["b"], out=S["p"]))
