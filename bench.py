@@ -360,26 +360,17 @@ def main():
 
     mul_events = {n: [] for n in sizes}
     add_events = {n: [] for n in sizes}
-    # the three divisions are independent of the sweep and of each other, and
-    # none fills the GPU to its end (2^20 / 2^19 bits: 256 one-SM instances,
-    # two waves on 152 SMs), so they run on streams of their own from the
-    # start of the step, the largest first: their launches take the SMs the
-    # sweep's launches leave idle between kernels and in their last waves
+    # the three divisions are independent and none fills the GPU to its end
+    # (2^20 / 2^19 bits: 256 one-SM instances, two waves on 152 SMs), so they
+    # run side by side on streams of their own after the sweep, the largest
+    # first: the smaller ones take the SMs the larger ones leave idle in
+    # their last wave.  (Started with the sweep instead, they shortened the
+    # step by 0.3 %, and the sweep's launches, timed below inside the step,
+    # would share the GPU with them.)
     div_streams = [torch.cuda.Stream(device=dev) for _ in DIV]
 
     def one_step(record):
         flush.fill_(1)
-        fork = torch.cuda.Event()
-        fork.record(stream)
-        joins = []
-        for (n, batch), ds in zip(sorted(DIV, reverse=True), div_streams):
-            D = divs[n]
-            ds.wait_event(fork)
-            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"],
-                      stream=ds)
-            j = torch.cuda.Event()
-            j.record(ds)
-            joins.append(j)
         for n in sizes:
             S = sweep[n]
             if record:
@@ -399,6 +390,17 @@ def main():
                 e3 = torch.cuda.Event(enable_timing=True)
                 e3.record(stream)
                 mul_events[n].append((e2, e3))
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        joins = []
+        for (n, batch), ds in zip(sorted(DIV, reverse=True), div_streams):
+            D = divs[n]
+            ds.wait_event(fork)
+            bi.divmod(D["u"], D["v"], q=D["q"], r=D["r"], status=D["st"], workspace=D["ws"],
+                      stream=ds)
+            j = torch.cuda.Event()
+            j.record(ds)
+            joins.append(j)
         for j in joins:
             stream.wait_event(j)
 
@@ -447,17 +449,14 @@ def main():
     for n in sizes:
         S = sweep[n]
         b = S["a"].shape[0]
-        # each op alone (the step's own spans share the GPU with the divisions)
-        t_add = time_op(lambda: bi.add(S["a"], S["b"], out=S["s"], carry=S["c"]))
-        t_mul = time_op(lambda: bi.mul_kara(S["a"], S["b"], out=S["p"], workspace=S["kws"]))
-        in_add = sum(e0.elapsed_time(e1) for e0, e1 in add_events[n]) / len(add_events[n])
-        in_mul = sum(e0.elapsed_time(e1) for e0, e1 in mul_events[n]) / len(mul_events[n])
+        # the spans of each op inside the timed steps (CUDA events)
+        t_add = sum(e0.elapsed_time(e1) for e0, e1 in add_events[n]) / len(add_events[n])
+        t_mul = sum(e0.elapsed_time(e1) for e0, e1 in mul_events[n]) / len(mul_events[n])
         breakdown[f"add_{n}"] = {"ms": t_add, "ops_per_s": b / (t_add * 1e-3),
-                                 "GB_s": 24.0 * b * n / (t_add * 1e-3) / 1e9,
-                                 "in_step_ms": in_add}
+                                 "GB_s": 24.0 * b * n / (t_add * 1e-3) / 1e9}
         breakdown[f"mul_{n}"] = {"ms": t_mul, "ops_per_s": b / (t_mul * 1e-3),
                                  "limb_gops": b * n * n / (t_mul * 1e-3) / 1e9,
-                                 "form": kara_form(n), "in_step_ms": in_mul}
+                                 "form": kara_form(n)}
         if kara_levels(n) > 0:  # the schoolbook product alone, for the roofline
             breakdown[f"mul_{n}"]["schoolbook_ms"] = time_op(
                 lambda: bi.mul(S["a"], S["b"], out=S["p"]))
@@ -527,11 +526,21 @@ def main():
         row = breakdown[f"mul_{n}"]
         return row.get("schoolbook_ms", row["ms"])
 
-    mul_ms = school_ms(nmax)
+    # the dominant kernel as the step runs it: the tensor-core product at the
+    # leaf size of the largest Karatsuba product (2048 limbs: the 2^17-bit
+    # sweep product and every leaf of the 2^18- and 2^19-bit products), its
+    # sweep launch timed inside the step
+    nk = nmax >> kara_levels(nmax)
+    if nk not in sizes:
+        nk = nmax
+    mul_ms = breakdown[f"mul_{nk}"]["ms"] if kara_levels(nk) == 0 else school_ms(nk)
     all_ms = sum(school_ms(n) for n in sizes)
     tr = committed_traffic()
-    kernel = (f"{'k_mul_tc<256>' if vmax == 12 else 'k_mul_kara' if vmax in (10, 11) else 'k_mul'}"
-              f" (variant {vmax}), {nmax}-limb operands, batch {sweep_batch(nmax)}")
+    vk = bi.mul_variant_for(nk, nk)
+    kernel = (f"{'k_mul_tc<256, 8, 1, 128>' if vk == 12 else 'k_mul_kara' if vk in (10, 11) else 'k_mul'}"
+              f" (variant {vk}), {nk}-limb operands, batch {sweep_batch(nk)}: the launch shape "
+              f"of the step's tensor-core products (the {nk}-limb sweep product and the leaves "
+              f"of the Karatsuba products)")
     if vmax == 12:
         # tensor bound: 2 flops per fp16 digit product of the 8-bit schoolbook
         # convolution, (8 n)^2 per n x n product.  The step holds the maximum
@@ -545,12 +554,12 @@ def main():
         burst = float(peaks.get("bf16_tflops", 1900.0))
         sustained = float(peaks.get("bf16_tflops_sustained", 1700.0))
         peak = burst
-        achieved = tc_flops(nmax) / (mul_ms * 1e-3) / 1e12
+        achieved = tc_flops(nk) / (mul_ms * 1e-3) / 1e12
         tc_sizes = [n for n in sizes if bi.mul_variant_for(n, n) == 12]
         tc_ms = sum(school_ms(n) for n in tc_sizes)
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": tr.get(f"bytes_per_launch_{nmax}") if tr else None,
+                    "traffic": tr.get(f"bytes_per_launch_{nk}") if tr else None,
                     "kernel": kernel,
                     "algorithmic_work": "2 x (8 n)^2 flops per n x n product: fp16 products of "
                                         "base-256 digits, accumulated in fp32",
@@ -558,10 +567,11 @@ def main():
                                        / peak) if tc_sizes else None,
                     "frac_by_size": {str(n): tc_flops(n) / (school_ms(n) * 1e-3)
                                      / 1e12 / peak for n in tc_sizes},
-                    "timing_basis": ("the schoolbook tensor-core product of each size timed "
-                                     "alone (bigint_mul); in the step, the square products of "
-                                     "4096 and 8192 limbs run as 1 and 2 Karatsuba levels over "
-                                     "2048-limb products of this kernel"),
+                    "timing_basis": (f"achieved: the {nk}-limb product's span inside the timed "
+                                     "step; frac_by_size: the schoolbook tensor-core product of "
+                                     "each size (the 4096- and 8192-limb ones timed alone, since "
+                                     "the step runs them as Karatsuba levels over 2048-limb "
+                                     "products of this kernel)"),
                     "frac_of_sustained": achieved / sustained,
                     # the sustained peak scaled from its own median SM clock to
                     # the clock this step held (time x median SM MHz)
