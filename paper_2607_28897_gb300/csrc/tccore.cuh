@@ -61,7 +61,9 @@
 // core's shallow instruction queue for most of a group, hence a warp of its
 // own); meanwhile the drain threads drain the other accumulator and build
 // the next group's Hankel core matrices (double buffered; each y digit of
-// the group recoded once into a staging run, the rows copied out of it).
+// the group recoded once into a staging run, the rows copied out of it),
+// then report that buffer and accumulator ready on an mbarrier, on which
+// the issuer waits before the next group.
 // NT = 256 (one CTA per SM, all of its tensor memory) serves large
 // products; NT = 128 (two CTAs per SM) and NT = 64 (three) keep several
 // issuers per SM for small ones, where an MMA's time is its A operand's
@@ -194,6 +196,27 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// One arrival (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Named barrier 2 over the first NTH threads of the CTA with an OR of v over
+// them: every participant gets the same answer.
+template <int NTH>
+__device__ __forceinline__ bool bar_or_drain(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 2, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(NTH)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
@@ -506,6 +529,8 @@ __device__ __forceinline__ void drain(uint32_t taddr, int cq, int lo, int hi, in
 // calling kernel).
 struct TcShared {
   uint64_t bars[2];   // mbarriers: MMAs of the group in accumulator b completed
+  uint64_t ready[2];  // mbarriers: Hankel buffer b built and accumulator b drained
+                      // for the next group there (one arrival per drain warp)
   uint64_t carry_hi;  // high word carried into the next tile's first limb
   uint32_t carry;     // carry bit carried into the next tile
   uint32_t borrow;    // borrow of the bias subtraction carried into the next tile
@@ -519,7 +544,9 @@ struct TcCtx {
   TcShared *sh;
   uint32_t *scr;      // BLK_SCRATCH_WORDS words for the carry scans
   uint32_t phase;     // bit b: parity of the next completion of bars[b]
-  uint32_t pending;   // bit b: a commit on bars[b] not yet waited for
+  uint32_t pending;   // bit b: a commit on bars[b] not yet waited for (tc_product:
+                      // kept by the issuing thread only)
+  uint32_t rphase;    // issuing thread: parity of the next completion of ready[b]
   bool aborted;       // a wait hit its limit: no further products
 };
 
@@ -536,10 +563,13 @@ __device__ void tc_init(TcCtx &c, uint8_t *sm, TcShared *sh, uint32_t *scr) {
   c.scr = scr;
   c.phase = 0;
   c.pending = 0;
+  c.rphase = 0;
   c.aborted = false;
   if (threadIdx.x == 0) {
     mbar_init(smem_u32(&sh->bars[0]), 1);
     mbar_init(smem_u32(&sh->bars[1]), 1);
+    mbar_init(smem_u32(&sh->ready[0]), 2 * NT / 32);
+    mbar_init(smem_u32(&sh->ready[1]), 2 * NT / 32);
     fence_mbar_init();
   }
   if (threadIdx.x < 32) {
@@ -585,9 +615,12 @@ __device__ void tc_release(TcCtx &c) {
 // floor(out / B^(h - L0)) is floor(x y / B^h) or one more, and never wraps
 // while x y + B^h < B^nout.
 //
-// IW: one extra warp (the last) only issues MMAs; the issuing thread blocks
-// while the tensor core's queue is full, so on its own warp that wait does
-// not hold up any drain or Hankel build.  Without IW thread 0 issues.
+// IW (required): one extra warp (the last) only issues MMAs; the issuing
+// thread blocks while the tensor core's queue is full, so on its own warp
+// that wait does not hold up any drain or Hankel build.  It waits for the
+// drain warps only through the ready[] mbarriers (one per Hankel buffer and
+// accumulator), never at a block barrier inside a tile: a block barrier
+// per group held it ~0.6K cycles per group after the queue had emptied.
 //
 // Split mode (SPLIT, lo = 0): only tile `tile` (columns [NT tile, NT tile +
 // W)) is computed, with no carry in, and neither the bias nor x's top bit is
@@ -618,9 +651,10 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   constexpr int S = 128 / KB, R = KB / 8;      // rows per coefficient, limbs per column
   static_assert(G * KB <= 1024, "partial sums of a group stay within 2^24");
   static_assert(KB == 128 || !SPLIT, "split tiles with 128-digit columns only");
+  static_assert(IW, "the MMAs are issued by a warp of their own");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool issuer = IW ? tid == DRAIN : tid == 0;
-  const bool worker = !IW || tid < DRAIN;
+  const bool issuer = tid == DRAIN;
+  const bool worker = tid < DRAIN;
   const Layout Ly = layout<NT, G, XC, KB>(nx, ny);
   uint8_t *sm = c.sm;
   const uint32_t sbase = c.sbase;
@@ -629,6 +663,7 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
   uint32_t *Cs = reinterpret_cast<uint32_t *>(sm + Ly.cs);
   uint32_t *His = reinterpret_cast<uint32_t *>(sm + Ly.his);
   const uint32_t mb[2] = {smem_u32(&c.sh->bars[0]), smem_u32(&c.sh->bars[1])};
+  const uint32_t rb[2] = {smem_u32(&c.sh->ready[0]), smem_u32(&c.sh->ready[1])};
   const int q = warp & 3, cq = warp >> 2;  // TMEM lane quadrant, 64-column slice
   const uint32_t t_lane = c.tmem + ((uint32_t)(32 * q) << 16);
   int acc[64];
@@ -674,53 +709,77 @@ __device__ __forceinline__ bool tc_product(TcCtx &c, const uint64_t *x, int nx, 
       fence_async_smem();
       __syncthreads();
       bool bad = false;
-      for (int gi = 0; gi < NG; gi++) {
-        const int b = gi & 1;
-        const int ea = e_lo + gi * G, eb = ea + G - 1 < e_hi ? ea + G - 1 : e_hi;
-        if (issuer)
-          issue_group<KB>(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a,
-                          z_a, lbo_b, c0, W, ea, eb, Ly.mx, mb[b]);
-        c.pending |= 1u << b;
-        // the next group's y limbs are fetched before the wait
-        const bool more = gi + 1 < NG && worker;
-        HankLimbs hv{0ull, 0ull};
-        if (more) {
-          const int na = ea + G;
-          hv = hank_load<G, KB>(y, ny, na + G - 1 < e_hi ? na + G - 1 : e_hi, tid);
-        }
-        if (gi >= 1) {  // group gi-1 used the other buffers
-          const int ob = b ^ 1;
-          if (worker && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) {
-            bad = true;  // still pending: tc_release waits for it
-          } else {
-            c.phase ^= 1u << ob;
-            c.pending &= ~(1u << ob);
+      auto last_block = [&](int gi) {
+        return e_lo + gi * G + G - 1 < e_hi ? e_lo + gi * G + G - 1 : e_hi;
+      };
+      if (issuer) {
+        // group gi into accumulator and Hankel buffer gi & 1, as soon as the
+        // drain warps report that buffer built and that accumulator drained
+        // (from the second group on): no block barrier between groups, so
+        // the tensor core's queue is refilled while it still holds work
+        for (int gi = 0; gi < NG; gi++) {
+          const int b = gi & 1;
+          if (gi >= 1) {
+            if (!mbar_wait(rb[b], (c.rphase >> b) & 1u)) { bad = true; break; }
+            c.rphase ^= 1u << b;
           }
-          tc_fence_after();
-          int slo, shi;
-          group_span<KB>(c0, W, ea - G, ea - 1, Ly.mx, slo, shi);
-          if (worker) drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
+          if (gi >= 2) {  // drained: group gi - 2 has completed
+            c.phase ^= 1u << b;
+            c.pending &= ~(1u << b);
+          }
+          issue_group<KB>(c.tmem + (uint32_t)(b * NT), b ? sbase + Ly.h1 : sbase + Ly.h0, xs_a,
+                          z_a, lbo_b, c0, W, e_lo + gi * G, last_block(gi), Ly.mx, mb[b]);
+          c.pending |= 1u << b;
         }
-        if (more) hank_build<G, DRAIN, KB>(b ? sm + Ly.h0 : sm + Ly.h1, sm + Ly.st, hv, tid);
-        tc_fence_before();
-        fence_async_smem();
-        if (__syncthreads_or(bad)) { c.aborted = true; return false; }
-      }
-      const int lb = (NG - 1) & 1;
-      if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) {  // all: TMEM reuse below
-        bad = true;  // still pending: tc_release waits for it
-      } else {
-        c.phase ^= 1u << lb;
-        c.pending &= ~(1u << lb);
-      }
-      tc_fence_after();
-      {
-        int slo, shi;
-        group_span<KB>(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
-        if (worker) drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
+      } else if (worker) {
+        for (int gi = 0; gi < NG; gi++) {
+          const int ob = (gi & 1) ^ 1;
+          const bool more = gi + 1 < NG;
+          // the next group's y limbs are fetched before the wait
+          HankLimbs hv{0ull, 0ull};
+          if (more) hv = hank_load<G, KB>(y, ny, last_block(gi + 1), tid);
+          if (gi >= 1 && !mbar_wait(mb[ob], (c.phase >> ob) & 1u)) bad = true;
+          // all drain threads agree; past this barrier every one of them has
+          // finished the previous iteration (the Hankel staging run is free)
+          if (bar_or_drain<DRAIN>(bad)) { bad = true; break; }
+          if (gi >= 1) {  // group gi - 1 (accumulator ob): drain
+            c.phase ^= 1u << ob;
+            tc_fence_after();
+            int slo, shi;
+            group_span<KB>(c0, W, e_lo + (gi - 1) * G, last_block(gi - 1), Ly.mx, slo, shi);
+            drain(t_lane + (uint32_t)(ob * NT), cq, slo, shi, acc);
+          }
+          if (more) {  // group gi + 1 into Hankel buffer ob, then report it
+            hank_build<G, DRAIN, KB>(ob ? sm + Ly.h1 : sm + Ly.h0, sm + Ly.st, hv, tid);
+            tc_fence_before();
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(rb[ob]);
+          }
+        }
+        if (!bad) {
+          const int lb = (NG - 1) & 1;
+          if (!mbar_wait(mb[lb], (c.phase >> lb) & 1u)) {
+            bad = true;
+          } else {
+            c.phase ^= 1u << lb;
+            tc_fence_after();
+            int slo, shi;
+            group_span<KB>(c0, W, e_lo + (NG - 1) * G, e_hi, Ly.mx, slo, shi);
+            drain(t_lane + (uint32_t)(lb * NT), cq, slo, shi, acc);
+          }
+        }
       }
       tc_fence_before();
+      // an abort leaves the issuing thread's pending bits for tc_release
       if (__syncthreads_or(bad)) { c.aborted = true; return false; }
+      tc_fence_after();
+      if (issuer) {  // the last one or two groups have completed (drained above)
+        for (int gi = NG >= 2 ? NG - 2 : 0; gi < NG; gi++) {
+          c.phase ^= 1u << (gi & 1);
+          c.pending &= ~(1u << (gi & 1));
+        }
+      }
     }
 
     // ---- column sums -> limbs of this tile (low words to out, high words to His)
