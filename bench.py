@@ -901,9 +901,10 @@ def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
             times.append(e0.elapsed_time(e1))
         return ranks.max_over_ranks(min(times), dist, dev)
 
-    # about a second of the persistent form first, so that the GPU's clocks
-    # have settled under load before the timed passes (a first pass after a
-    # stretch of low load measured 6-12 % slower for every form)
+    # SM clocks sampled from here to the last timed pass; about a second of
+    # the persistent form first, so that they have settled under load
+    clk = ClockSampler(dev.index if dev is not None and dev.index is not None else 0)
+    clk.start()
     t_end = time.perf_counter() + 1.0
     while time.perf_counter() < t_end:
         B.launch(pool, out, st, mode=bi.BATCH_PERSISTENT)
@@ -926,6 +927,7 @@ def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
         with torch.cuda.graph(g, stream=s):
             B.launch(pool, out, st, mode=mode, stream=s)
     t_graph = best_of(lambda: g.replay(), reps)
+    clocks = clk.stop()
     same = same and bool(torch.equal(out, ref))
     bad_status = int((st[:len(ops)] < 0).sum().item()) if len(ops) else 0
     del pool, out, st, ref, g
@@ -938,7 +940,7 @@ def batched_block(torch, bi, count, reps, rank=0, world=1, dist=None, dev=None):
             "persistent_ms": t_pers, "steps_ms": t_steps,
             "graph_form": "steps" if mode == bi.BATCH_STEPS else "persistent",
             "tuned_graph_ms": t_graph,
-            "tuned_threads": threads, "speedup_vs_per_class": t_class / best,
+            "tuned_threads": threads, "speedup_vs_per_class": t_class / best, "clocks": clocks,
             "results_identical_across_forms": same, "negative_statuses": bad_status,
             "scaling": "strong" if world > 1 else None,
             "ranks": world}
