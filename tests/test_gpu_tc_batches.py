@@ -74,3 +74,23 @@ def test_kara_batches(bi, orc, n, count):
     assert np.array_equal(k, school)
     rows = [0, 151, count - 1]
     assert np.array_equal(k[rows], orc.batch_mul(a[rows], b[rows]))
+
+
+@pytest.mark.parametrize("n,count", [(2048, 160), (4096, 160), (8192, 160), (1500, 200)])
+def test_more_products_than_sms_against_fewer(bi, orc, n, count):
+    """A batch with more products than SMs (persistent CTAs that compute
+    several products in turn, reusing their shared memory and tensor memory)
+    equals, product by product, the same products in a batch of at most one
+    per SM, and sampled products equal the oracle's; multi-tile products
+    (4096 and 8192 limbs) included."""
+    from paper_2607_28897_gb300 import inputs
+
+    a = inputs.limbs(2000 + n, count, n)
+    b = inputs.limbs(2100 + n, count, n)
+    da, db = to_dev(a), to_dev(b)
+    many = to_host(bi.mul(da, db))
+    few = to_host(bi.mul(da[:150].contiguous(), db[:150].contiguous()))
+    bi.check_timeout()
+    assert np.array_equal(many[:150], few)
+    rows = [0, 149, 151, count - 1]
+    assert np.array_equal(many[rows], orc.batch_mul(a[rows], b[rows]))
