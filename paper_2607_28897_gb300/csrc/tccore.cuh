@@ -629,8 +629,9 @@ __device__ void tc_release(TcCtx &c) {
 // thread blocks while the tensor core's queue is full, so on its own warp
 // that wait does not hold up any drain or Hankel build.  It waits for the
 // drain warps only through the ready[] mbarriers (one per Hankel buffer and
-// accumulator), never at a block barrier inside a tile: a block barrier
-// per group held it ~0.6K cycles per group after the queue had emptied.
+// accumulator), never at a block barrier inside a tile (with a block
+// barrier per group it spent ~0.65K cycles per group outside the MMA issue,
+// by clock64 probes).
 //
 // Split mode (SPLIT, lo = 0): only tile `tile` (columns [NT tile, NT tile +
 // W)) is computed, with no carry in, and neither the bias nor x's top bit is
